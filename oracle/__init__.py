@@ -1,0 +1,274 @@
+"""Plain FP64 CPU oracle for the d-dimensional soft-sphere MD hot path.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference arm of ``bench.py`` may import this package.  The
+product path (the CUDA library and its Python binding) never imports, links or
+executes anything here, and this package imports nothing from the product.
+
+The arithmetic lives in ``hdmd_oracle.c`` (serial C, double precision, every
+function citing the passage of arXiv:2112.12271 it follows).  This module
+compiles it with gcc on first use and wraps it with ctypes + numpy.  Arrays
+are row-major ``x[N, d]``.
+
+Parity status of each function (what pins it, see tests/test_oracle_pins.py):
+  sphere_volume, n_cell, cell_index ... closed forms, hand-built examples
+  neighbors_brute / neighbors_cells .. each other, hypercubic-lattice counts
+                                       (2d, 2d^2), symmetry, O(N^2) brute force
+  forces ............................. two-body closed form, central finite
+                                       differences of E, Newton's third law,
+                                       virial = -sum x.grad U
+  md_steps ........................... time reversibility, energy drift ~ dt^2,
+                                       head-on two-body collision
+  fire ............................... |F|max < 1e-10, E -> 0 below jamming,
+                                       two spheres relax to contact
+  swap ............................... brute dE, equal diameters always
+                                       accepted, exact detailed balance (3 atoms)
+  philox4x32_10 ...................... published known-answer vectors
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hdmd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, no FMA contraction) into oracle/_build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp.%d" % os.getpid()
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            i64, i32, dbl, vp = C.c_int64, C.c_int, C.c_double, C.c_void_p
+            lib.orc_sphere_volume.restype = dbl
+            lib.orc_sphere_volume.argtypes = [i32, dbl]
+            lib.orc_n_cell.restype = i32
+            lib.orc_n_cell.argtypes = [dbl, dbl]
+            lib.orc_cell_index.restype = i64
+            lib.orc_cell_index.argtypes = [i32, i32, vp]
+            lib.orc_min_image.restype = dbl
+            lib.orc_min_image.argtypes = [dbl, dbl]
+            for fn in (lib.orc_neighbors_brute, lib.orc_neighbors_cells):
+                fn.restype = i64
+                fn.argtypes = [i32, i64, dbl, vp, vp, dbl, i32, vp, vp, i64]
+            lib.orc_harmonic.restype = dbl
+            lib.orc_harmonic.argtypes = [dbl, dbl, dbl, C.POINTER(dbl)]
+            lib.orc_forces.restype = None
+            lib.orc_forces.argtypes = [i32, i64, dbl, vp, vp, dbl, vp, vp, vp,
+                                       C.POINTER(dbl), C.POINTER(dbl)]
+            lib.orc_kinetic.restype = dbl
+            lib.orc_kinetic.argtypes = [i32, i64, vp, vp]
+            lib.orc_md_steps.restype = i64
+            lib.orc_md_steps.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl,
+                                         dbl, i64, vp, vp]
+            lib.orc_fire.restype = i32
+            lib.orc_fire.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl, vp,
+                                     vp, vp]
+            lib.orc_swap.restype = i64
+            lib.orc_swap.argtypes = [i32, i64, dbl, vp, vp, vp, vp, dbl, dbl, i64, vp,
+                                     vp, vp]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
+            lib.orc_swap_draw.restype = None
+            lib.orc_swap_draw.argtypes = [C.c_uint64, i64, i64, i64, vp, vp]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------- geometry
+def sphere_volume(d: int, sigma: float) -> float:
+    """Eq. (2): volume of a d-sphere of diameter sigma."""
+    return _load().orc_sphere_volume(d, sigma)
+
+
+def n_cell(L: float, rc_max: float) -> int:
+    """Eq. (7): subcells per axis."""
+    return _load().orc_n_cell(L, rc_max)
+
+
+def cell_index(d: int, n: int, C_: np.ndarray) -> int:
+    """Eq. (9): linear subcell index, axis 1 most significant."""
+    c = np.ascontiguousarray(C_, dtype=np.int32)
+    return _load().orc_cell_index(d, n, _p(c))
+
+
+def min_image(dx: float, L: float) -> float:
+    return _load().orc_min_image(dx, L)
+
+
+# --------------------------------------------------------------- lists
+def _neighbors(fn, x, sigma, L, skin, global_cut):
+    x = _f64(x)
+    N, d = x.shape
+    sigma = _f64(sigma)
+    counts = np.zeros(N, dtype=np.int32)
+    tot = fn(d, N, L, _p(x), _p(sigma), skin, int(global_cut), _p(counts), None, 0)
+    if tot < 0:
+        raise ValueError("oracle neighbor build failed (%d)" % tot)
+    idx = np.zeros(max(tot, 1), dtype=np.int32)
+    tot2 = fn(d, N, L, _p(x), _p(sigma), skin, int(global_cut), _p(counts), _p(idx), tot)
+    assert tot2 == tot
+    return counts, idx[:tot]
+
+
+def neighbors_brute(x, sigma, L, skin, global_cut=False):
+    """Full Verlet lists by all-pairs search; (counts[N], idx[sum]) ascending."""
+    return _neighbors(_load().orc_neighbors_brute, x, sigma, L, skin, global_cut)
+
+
+def neighbors_cells(x, sigma, L, skin, global_cut=False):
+    """Full Verlet lists with the linked-subcell loop nest of Sec. II.C."""
+    return _neighbors(_load().orc_neighbors_cells, x, sigma, L, skin, global_cut)
+
+
+def lists_as_sets(counts, idx):
+    out, off = [], 0
+    for c in counts:
+        out.append(set(int(j) for j in idx[off:off + c]))
+        off += c
+    return out
+
+
+# --------------------------------------------------------------- forces
+def harmonic(r: float, s: float, eps: float = 1.0):
+    """(U, |f|/r) of the harmonic soft-sphere law."""
+    fr = C.c_double()
+    u = _load().orc_harmonic(r, s, eps, C.byref(fr))
+    return u, fr.value
+
+
+def forces(x, sigma, L, eps=1.0, lists=None):
+    """(F[N,d], E_pair, W) by brute force, or over full lists (counts, idx)."""
+    x = _f64(x)
+    N, d = x.shape
+    sigma = _f64(sigma)
+    F = np.zeros_like(x)
+    E, W = C.c_double(), C.c_double()
+    if lists is None:
+        cnt = idx = None
+    else:
+        cnt = np.ascontiguousarray(lists[0], dtype=np.int32)
+        idx = np.ascontiguousarray(lists[1], dtype=np.int32)
+        if idx.size == 0:
+            idx = np.zeros(1, dtype=np.int32)
+    _load().orc_forces(d, N, L, _p(x), _p(sigma), eps, _p(cnt), _p(idx), _p(F),
+                       C.byref(E), C.byref(W))
+    return F, E.value, W.value
+
+
+def kinetic(v, mass=None):
+    v = _f64(v)
+    N, d = v.shape
+    m = None if mass is None else _f64(mass)
+    return _load().orc_kinetic(d, N, _p(v), _p(m))
+
+
+# --------------------------------------------------------------- integrators
+def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None, F=None):
+    """Velocity Verlet in place on copies; returns dict(x, v, img, F, E, W, K, builds)."""
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    N, d = x.shape
+    sigma = _f64(sigma)
+    m = None if mass is None else _f64(mass)
+    img = np.zeros((N, d), dtype=np.int32) if img is None else np.array(img, dtype=np.int32)
+    if F is None:
+        F, _, _ = forces(x, sigma, L, eps, neighbors_brute(x, sigma, L, skin)
+                         if N <= 4096 else None)
+    F = _f64(F).copy()
+    th = np.zeros(3)
+    b = _load().orc_md_steps(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
+                             dt, int(nsteps), _p(F), _p(th))
+    return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b))
+
+
+FIRE_DEFAULTS = dict(dt0=0.005, dt_max=0.05, dt_min=1e-4, f_inc=1.1, f_dec=0.5,
+                     alpha0=0.25, f_alpha=0.99, f_tol=1e-10, n_delay=20, n_neg_max=2000,
+                     max_iter=1000000, initial_delay=1)
+
+
+class _FireParams(C.Structure):
+    _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("dt_min", C.c_double),
+                ("f_inc", C.c_double), ("f_dec", C.c_double), ("alpha0", C.c_double),
+                ("f_alpha", C.c_double), ("f_tol", C.c_double), ("n_delay", C.c_int64),
+                ("n_neg_max", C.c_int64), ("max_iter", C.c_int64),
+                ("initial_delay", C.c_int)]
+
+
+def fire(x, sigma, L, skin=0.3, eps=1.0, mass=None, **params):
+    """FIRE 2.0 minimisation; returns dict(x, F, E, fmax, iters, status, builds)."""
+    p = dict(FIRE_DEFAULTS)
+    p.update(params)
+    fp = _FireParams(**p)
+    x = _f64(x).copy()
+    N, d = x.shape
+    v = np.zeros_like(x)
+    F = np.zeros_like(x)
+    img = np.zeros((N, d), dtype=np.int32)
+    sigma = _f64(sigma)
+    m = None if mass is None else _f64(mass)
+    out = np.zeros(4)
+    st = _load().orc_fire(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
+                          C.addressof(fp), _p(F), _p(out))
+    return dict(x=x, v=v, img=img, F=F, E=out[1], fmax=out[2], iters=int(out[0]),
+                status=int(st), builds=int(out[3]))
+
+
+# --------------------------------------------------------------- SWAP
+def swap(x, sigma, L, T, pairs, uniforms, eps=1.0, mass=None, v=None):
+    """Serial SWAP pass; returns dict(sigma, mass, v, accepted[npairs], naccepted)."""
+    x = _f64(x)
+    N, d = x.shape
+    sigma = _f64(sigma).copy()
+    m = None if mass is None else _f64(mass).copy()
+    vv = None if v is None else _f64(v).copy()
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    u = _f64(uniforms)
+    acc = np.zeros(len(pairs), dtype=np.int8)
+    n = _load().orc_swap(d, N, L, _p(x), _p(sigma), _p(m), _p(vv), eps, T, len(pairs),
+                         _p(pairs), _p(u), _p(acc))
+    return dict(sigma=sigma, mass=m, v=vv, accepted=acc.astype(bool), naccepted=int(n))
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def swap_draw(seed: int, sweep: int, npairs: int, N: int):
+    """The seeded candidate pairs and uniforms of one SWAP pass."""
+    pairs = np.zeros((npairs, 2), dtype=np.int32)
+    u = np.zeros(npairs)
+    _load().orc_swap_draw(seed, sweep, npairs, N, _p(pairs), _p(u))
+    return pairs, u

@@ -1,0 +1,650 @@
+/*
+ * hdmd_oracle.c -- plain, slow, FP64 CPU oracle for the hot path of
+ * d-dimensional soft-sphere molecular dynamics (Hoy & Interiano-Alberto,
+ * "Efficient d-dimensional molecular dynamics simulations for studies of the
+ * glass-jamming transition", arXiv:2112.12271).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load or call this file.  The CUDA library
+ * never links it, and the two share no code, header, table or constant.
+ *
+ * Everything here is double precision, serial and written for a reader who
+ * wants to check it against the paper by eye:
+ *   - minimum-image distances under periodic boundaries in all d axes
+ *     (Sec. II.A, last paragraph; box centred at the origin);
+ *   - Verlet lists two ways: brute force over all pairs (the plain
+ *     definition) and the paper's linked-subcell loop nest (Sec. II.C, Fig. 1,
+ *     Eqs. (7)-(9)); each checks the other;
+ *   - the harmonic soft-sphere pair law U = (eps/2)(1 - r/s_ij)^2 for
+ *     r < s_ij with s_ij = (s_i + s_j)/2 (the Lorentz mixing rule of
+ *     Sec. II.A; the paper says the radial law is a user choice);
+ *   - kick-drift-kick velocity Verlet (Sec. II.B);
+ *   - FIRE 2.0 with the semi-implicit Euler integrator (Sec. II.B; the
+ *     paper names the method but prints neither steps nor constants, so the
+ *     steps follow the published FIRE 2.0 algorithm, see orc_fire);
+ *   - serial SWAP Monte Carlo with Eqs. (10)-(11) (Sec. II.D);
+ *   - the Philox4x32-10 counter-based generator (Salmon et al., SC'11) used
+ *     to draw SWAP pairs and Metropolis uniforms from a seed.
+ *
+ * Readings of points the paper leaves open are stated at each function.
+ * Positions are row-major x[i*d + k] with every coordinate in [-L/2, L/2).
+ * Build with -ffp-contract=off so that x86 and Arm give the same bits.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXD 16
+
+/* ------------------------------------------------------------------ */
+/* geometry                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Volume of a d-dimensional sphere of diameter sigma, Eq. (2). */
+double orc_sphere_volume(int d, double sigma)
+{
+    return pow(M_PI, 0.5 * d) * pow(sigma, d) / (pow(2.0, d) * tgamma(1.0 + 0.5 * d));
+}
+
+/* Subcells per axis, Eq. (7): floor(L / (largest diameter + skin)). */
+int orc_n_cell(double L, double rc_max)
+{
+    return (int)floor(L / rc_max);
+}
+
+/* Linear subcell index of Eq. (9): I = sum_k C_k n^(d-k), axis 1 most
+ * significant (k counts from 1 in the paper, from 0 here). */
+int64_t orc_cell_index(int d, int n, const int *C)
+{
+    int64_t I = 0;
+    for (int k = 0; k < d; ++k) I = I * n + C[k];
+    return I;
+}
+
+/* Subcell coordinate of a position along one axis: the subcell whose
+ * centre is given by Eq. (8).  Clamped against round-off at x = L/2. */
+static int cell_coord(double x, double L, int n)
+{
+    double Lsc = L / n;
+    int c = (int)floor((x + 0.5 * L) / Lsc);
+    if (c < 0) c = 0;
+    if (c > n - 1) c = n - 1;
+    return c;
+}
+
+/* Minimum-image separation along one axis (periodic in every axis). */
+double orc_min_image(double dx, double L)
+{
+    return dx - L * rint(dx / L);
+}
+
+/* Squared minimum-image distance between atoms i and j. */
+static double dist2(int d, double L, const double *x, int64_t i, int64_t j)
+{
+    double r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double dx = orc_min_image(x[j * d + k] - x[i * d + k], L);
+        r2 += dx * dx;
+    }
+    return r2;
+}
+
+/* Verlet-list radius for the pair (i, j).  The paper's r_c^max is the
+ * largest interaction range plus the skin (Sec. II.C).  Reading: the list
+ * keeps a pair when r < s_ij + skin (per pair, mode 0) or r < s_max + skin
+ * (one global radius, mode 1). */
+static double list_radius(double si, double sj, double skin, int global_cut, double smax)
+{
+    return global_cut ? smax + skin : 0.5 * (si + sj) + skin;
+}
+
+static double max_of(const double *a, int64_t n)
+{
+    double m = -INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+        if (a[i] > m) m = a[i];
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Verlet lists                                                         */
+/* ------------------------------------------------------------------ */
+
+/* Full Verlet lists by brute force over all pairs (the plain definition):
+ * j is in VL(i) iff j != i and |x_j - x_i|^2 < rc_ij^2 with minimum image.
+ * counts[N] receives the list lengths; when idx is non-NULL it receives the
+ * lists back to back, each in ascending j, and must hold cap entries.
+ * Returns the total number of entries, or -1 if idx is too small. */
+int64_t orc_neighbors_brute(int d, int64_t N, double L, const double *x,
+                            const double *sigma, double skin, int global_cut,
+                            int32_t *counts, int32_t *idx, int64_t cap)
+{
+    double smax = max_of(sigma, N);
+    int64_t tot = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t c = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double rc = list_radius(sigma[i], sigma[j], skin, global_cut, smax);
+            if (dist2(d, L, x, i, j) < rc * rc) {
+                if (idx) {
+                    if (tot >= cap) return -1;
+                    idx[tot] = (int32_t)j;
+                }
+                ++tot;
+                ++c;
+            }
+        }
+        counts[i] = c;
+    }
+    return tot;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Full Verlet lists with the paper's linked-subcell loop nest (Sec. II.C,
+ * Fig. 1): one outer loop over subcells I, the 3^d linked subcells of I
+ * enumerated on the fly from a base-3 counter, then the double loop over
+ * the atoms of I and of the linked subcell.  Reading for n_cell < 3: the
+ * offsets -1 and +1 name the same subcell when n_cell = 2, so each distinct
+ * subcell is visited once (offsets {0, +1}); n_cell must be >= 2, which
+ * holds whenever L >= 2 (s_max + skin).  Output as orc_neighbors_brute,
+ * each list sorted ascending.  Returns -2 if n_cell < 2. */
+int64_t orc_neighbors_cells(int d, int64_t N, double L, const double *x,
+                            const double *sigma, double skin, int global_cut,
+                            int32_t *counts, int32_t *idx, int64_t cap)
+{
+    double smax = max_of(sigma, N);
+    int n = orc_n_cell(L, smax + skin);
+    if (n < 2) return -2;
+    int64_t ncells = 1;
+    for (int k = 0; k < d; ++k) ncells *= n;
+
+    /* assign atoms to subcells (serial in the paper too) */
+    int64_t *cell = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *head = malloc(sizeof(int64_t) * (size_t)(ncells + 1));
+    int64_t *members = malloc(sizeof(int64_t) * (size_t)N);
+    memset(head, 0, sizeof(int64_t) * (size_t)(ncells + 1));
+    for (int64_t i = 0; i < N; ++i) {
+        int C[ORC_MAXD];
+        for (int k = 0; k < d; ++k) C[k] = cell_coord(x[i * d + k], L, n);
+        cell[i] = orc_cell_index(d, n, C);
+        head[cell[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncells; ++c) head[c + 1] += head[c];
+    {
+        int64_t *fill = malloc(sizeof(int64_t) * (size_t)ncells);
+        memcpy(fill, head, sizeof(int64_t) * (size_t)ncells);
+        for (int64_t i = 0; i < N; ++i) members[fill[cell[i]]++] = i;
+        free(fill);
+    }
+
+    /* per-atom lists, collected in atom order afterwards */
+    int32_t **lst = calloc((size_t)N, sizeof(int32_t *));
+    int32_t *len = calloc((size_t)N, sizeof(int32_t));
+    int32_t *capi = calloc((size_t)N, sizeof(int32_t));
+
+    int64_t nstencil = 1;
+    for (int k = 0; k < d; ++k) nstencil *= 3;
+
+    for (int64_t I = 0; I < ncells; ++I) {
+        int C[ORC_MAXD];
+        int64_t rem = I;
+        for (int k = d - 1; k >= 0; --k) { C[k] = (int)(rem % n); rem /= n; }
+        for (int64_t s = 0; s < nstencil; ++s) {
+            /* base-3 digits of s, axis 1 most significant: offset = digit-1 */
+            int off[ORC_MAXD], skip = 0;
+            int64_t t = s;
+            for (int k = d - 1; k >= 0; --k) { off[k] = (int)(t % 3) - 1; t /= 3; }
+            for (int k = 0; k < d; ++k)
+                if (n == 2 && off[k] == -1) skip = 1; /* same subcell as +1 */
+            if (skip) continue;
+            int CJ[ORC_MAXD];
+            for (int k = 0; k < d; ++k) CJ[k] = ((C[k] + off[k]) % n + n) % n;
+            int64_t J = orc_cell_index(d, n, CJ);
+            for (int64_t a = head[I]; a < head[I + 1]; ++a) {
+                int64_t i = members[a];
+                for (int64_t b = head[J]; b < head[J + 1]; ++b) {
+                    int64_t j = members[b];
+                    if (j == i) continue;
+                    double rc = list_radius(sigma[i], sigma[j], skin, global_cut, smax);
+                    if (dist2(d, L, x, i, j) < rc * rc) {
+                        if (len[i] == capi[i]) {
+                            capi[i] = capi[i] ? 2 * capi[i] : 16;
+                            lst[i] = realloc(lst[i], sizeof(int32_t) * (size_t)capi[i]);
+                        }
+                        lst[i][len[i]++] = (int32_t)j;
+                    }
+                }
+            }
+        }
+    }
+
+    int64_t tot = 0;
+    int overflow = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        qsort(lst[i], (size_t)len[i], sizeof(int32_t), cmp_i32);
+        counts[i] = len[i];
+        if (idx) {
+            if (tot + len[i] > cap) overflow = 1;
+            else memcpy(idx + tot, lst[i], sizeof(int32_t) * (size_t)len[i]);
+        }
+        tot += len[i];
+        free(lst[i]);
+    }
+    free(lst); free(len); free(capi); free(cell); free(head); free(members);
+    return overflow ? -1 : tot;
+}
+
+/* ------------------------------------------------------------------ */
+/* pair law, forces, energy, virial                                     */
+/* ------------------------------------------------------------------ */
+
+/* Harmonic soft spheres: U = (eps/2)(1 - r/s)^2 for r < s, else 0.  The
+ * force on i from j is (eps/s)(1 - r/s) along (x_i - x_j)/r; *fr receives
+ * that magnitude divided by r (0 at r = 0, a measure-zero guard).  Returns U. */
+double orc_harmonic(double r, double s, double eps, double *fr)
+{
+    if (r >= s) { *fr = 0.0; return 0.0; }
+    double g = 1.0 - r / s;
+    *fr = (r > 0.0) ? (eps / s) * g / r : 0.0;
+    return 0.5 * eps * g * g;
+}
+
+/* Pair forces F[N*d], pair energy E = sum_{i<j} U_ij and virial
+ * W = sum_{i<j} (x_i - x_j).f_ij.  With counts == NULL every pair i<j is
+ * visited (brute force); otherwise counts/idx hold full Verlet lists (as
+ * produced above) and each ordered pair contributes half of E and W. */
+void orc_forces(int d, int64_t N, double L, const double *x, const double *sigma,
+                double eps, const int32_t *counts, const int32_t *idx,
+                double *F, double *E, double *W)
+{
+    double e = 0.0, w = 0.0;
+    memset(F, 0, sizeof(double) * (size_t)(N * d));
+    if (!counts) {
+        for (int64_t i = 0; i < N; ++i) {
+            for (int64_t j = i + 1; j < N; ++j) {
+                double dx[ORC_MAXD], r2 = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    dx[k] = orc_min_image(x[i * d + k] - x[j * d + k], L);
+                    r2 += dx[k] * dx[k];
+                }
+                double s = 0.5 * (sigma[i] + sigma[j]), fr;
+                double r = sqrt(r2);
+                double u = orc_harmonic(r, s, eps, &fr);
+                if (u == 0.0 && fr == 0.0) continue;
+                for (int k = 0; k < d; ++k) {
+                    F[i * d + k] += fr * dx[k];
+                    F[j * d + k] -= fr * dx[k];
+                }
+                e += u;
+                w += fr * r2;
+            }
+        }
+    } else {
+        int64_t off = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            for (int32_t a = 0; a < counts[i]; ++a) {
+                int64_t j = idx[off + a];
+                double dx[ORC_MAXD], r2 = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    dx[k] = orc_min_image(x[i * d + k] - x[j * d + k], L);
+                    r2 += dx[k] * dx[k];
+                }
+                double s = 0.5 * (sigma[i] + sigma[j]), fr;
+                double r = sqrt(r2);
+                double u = orc_harmonic(r, s, eps, &fr);
+                for (int k = 0; k < d; ++k) F[i * d + k] += fr * dx[k];
+                e += 0.5 * u;
+                w += 0.5 * fr * r2;
+            }
+            off += counts[i];
+        }
+    }
+    *E = e;
+    *W = w;
+}
+
+/* Kinetic energy K = (1/2) sum m v^2. */
+double orc_kinetic(int d, int64_t N, const double *v, const double *mass)
+{
+    double k = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double m = mass ? mass[i] : 1.0, s = 0.0;
+        for (int c = 0; c < d; ++c) s += v[i * d + c] * v[i * d + c];
+        k += 0.5 * m * s;
+    }
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* neighbor-list bookkeeping shared by the MD and FIRE loops            */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t *counts, *idx;
+    int64_t cap;
+    double *x0;      /* positions at the last build */
+    int64_t builds;
+} orc_vl;
+
+/* Build the list the way the paper does: linked subcells when
+ * n_cell > 3, the all-pairs routine otherwise (Sec. II.C, last paragraph). */
+static void vl_build(orc_vl *vl, int d, int64_t N, double L, const double *x,
+                     const double *sigma, double skin)
+{
+    double smax = max_of(sigma, N);
+    int n = orc_n_cell(L, smax + skin);
+    int64_t (*fn)(int, int64_t, double, const double *, const double *, double, int,
+                  int32_t *, int32_t *, int64_t) =
+        n > 3 ? orc_neighbors_cells : orc_neighbors_brute;
+    if (!vl->counts) vl->counts = malloc(sizeof(int32_t) * (size_t)N);
+    /* first pass counts, second pass fills */
+    int64_t tot = fn(d, N, L, x, sigma, skin, 0, vl->counts, NULL, 0);
+    if (tot + 1 > vl->cap) {
+        vl->cap = tot + tot / 2 + 16;
+        vl->idx = realloc(vl->idx, sizeof(int32_t) * (size_t)vl->cap);
+    }
+    fn(d, N, L, x, sigma, skin, 0, vl->counts, vl->idx, vl->cap);
+    if (!vl->x0) vl->x0 = malloc(sizeof(double) * (size_t)(N * d));
+    memcpy(vl->x0, x, sizeof(double) * (size_t)(N * d));
+    vl->builds++;
+}
+
+/* Rebuild trigger.  Reading of Sec. II.C: the paper's rule (0.1 % of atoms
+ * moved s/2, or any atom moved s) can miss a pair closing from both sides,
+ * so the oracle rebuilds as soon as 2 max_i |x_i - x_i(build)| > skin, which
+ * keeps every list exact. */
+static int vl_needs_rebuild(const orc_vl *vl, int d, int64_t N, double L,
+                            const double *x, double skin)
+{
+    double dmax2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double dx = orc_min_image(x[i * d + k] - vl->x0[i * d + k], L);
+            s += dx * dx;
+        }
+        if (s > dmax2) dmax2 = s;
+    }
+    return 4.0 * dmax2 > skin * skin;
+}
+
+static void vl_free(orc_vl *vl)
+{
+    free(vl->counts); free(vl->idx); free(vl->x0);
+}
+
+/* Wrap one coordinate back into [-L/2, L/2), counting box crossings. */
+static double wrap(double x, double L, int32_t *img)
+{
+    if (x >= 0.5 * L) { x -= L; if (img) ++*img; }
+    else if (x < -0.5 * L) { x += L; if (img) --*img; }
+    return x;
+}
+
+/* ------------------------------------------------------------------ */
+/* velocity Verlet                                                      */
+/* ------------------------------------------------------------------ */
+
+/* nsteps of kick-drift-kick velocity Verlet in NVE (Sec. II.B: the
+ * leapfrog "kick-drift-kick" variant; no thermostat here).  One step:
+ *   v += (dt/2) F/m;  x += dt v, wrapped with image counts;
+ *   rebuild the Verlet list if the trigger fires;  F = F(x);
+ *   v += (dt/2) F/m.
+ * F must hold the forces at the incoming x and holds those at the outgoing
+ * x on return.  thermo[0..2] = E_pair, virial W, kinetic K at the end.
+ * Returns the number of list builds (the first one included). */
+int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *img,
+                     const double *sigma, const double *mass, double eps,
+                     double skin, double dt, int64_t nsteps, double *F,
+                     double *thermo)
+{
+    orc_vl vl = {0};
+    double E = 0.0, W = 0.0;
+    vl_build(&vl, d, N, L, x, sigma, skin);
+    for (int64_t step = 0; step < nsteps; ++step) {
+        for (int64_t i = 0; i < N; ++i) {
+            double m = mass ? mass[i] : 1.0;
+            for (int k = 0; k < d; ++k) {
+                v[i * d + k] += 0.5 * dt * F[i * d + k] / m;
+                x[i * d + k] += dt * v[i * d + k];
+                x[i * d + k] = wrap(x[i * d + k], L, img ? &img[i * d + k] : NULL);
+            }
+        }
+        if (vl_needs_rebuild(&vl, d, N, L, x, skin)) vl_build(&vl, d, N, L, x, sigma, skin);
+        orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
+        for (int64_t i = 0; i < N; ++i) {
+            double m = mass ? mass[i] : 1.0;
+            for (int k = 0; k < d; ++k) v[i * d + k] += 0.5 * dt * F[i * d + k] / m;
+        }
+    }
+    if (nsteps == 0) orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
+    thermo[0] = E;
+    thermo[1] = W;
+    thermo[2] = orc_kinetic(d, N, v, mass);
+    int64_t b = vl.builds;
+    vl_free(&vl);
+    return b;
+}
+
+/* ------------------------------------------------------------------ */
+/* FIRE 2.0                                                             */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double dt0, dt_max, dt_min, f_inc, f_dec, alpha0, f_alpha, f_tol;
+    int64_t n_delay, n_neg_max, max_iter;
+    int initial_delay;
+} orc_fire_params;
+
+/* FIRE 2.0 energy minimisation with the semi-implicit Euler integrator
+ * (Sec. II.B; Guenole et al., Comput. Mater. Sci. 175, 109584 (2020)).
+ * The paper cites the method and prints no step, so the steps below are
+ * the published algorithm, in order, with these readings:
+ *   - stop when max_i |F_i| < f_tol (per-atom Euclidean norm), tested before
+ *     each iteration; or after max_iter iterations; or after more than
+ *     n_neg_max consecutive P <= 0 steps;
+ *   - P = F.v over all atoms; on P > 0: Npos += 1, Nneg = 0, and after
+ *     n_delay such steps dt = min(f_inc dt, dt_max), alpha *= f_alpha;
+ *     on P <= 0: Npos = 0, Nneg += 1; unless still inside the initial
+ *     delay, dt = max(f_dec dt, dt_min) and alpha = alpha0; then
+ *     x -= (dt/2) v and v = 0;
+ *   - v += dt F/m; if P > 0, v = (1-alpha) v + alpha |v| F/|F| with norms
+ *     over all atoms; x += dt v; F = F(x).
+ * v is zeroed on entry.  out[0..3] = iterations, final E_pair, final
+ * max_i |F_i|, builds.  Returns 0 on convergence, 1 if max_iter was hit,
+ * 2 if the P <= 0 count ran out. */
+int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
+             const double *sigma, const double *mass, double eps, double skin,
+             const orc_fire_params *p, double *F, double *out)
+{
+    orc_vl vl = {0};
+    double E = 0.0, W = 0.0, dt = p->dt0, alpha = p->alpha0;
+    int64_t npos = 0, nneg = 0, it = 0;
+    int status = 1;
+    memset(v, 0, sizeof(double) * (size_t)(N * d));
+    vl_build(&vl, d, N, L, x, sigma, skin);
+    orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
+    for (;;) {
+        double fmax2 = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += F[i * d + k] * F[i * d + k];
+            if (s > fmax2) fmax2 = s;
+        }
+        if (sqrt(fmax2) < p->f_tol) { status = 0; break; }
+        if (it >= p->max_iter) { status = 1; break; }
+
+        double P = 0.0;
+        for (int64_t a = 0; a < N * d; ++a) P += F[a] * v[a];
+        if (P > 0.0) {
+            npos++;
+            nneg = 0;
+            if (npos > p->n_delay) {
+                dt = fmin(dt * p->f_inc, p->dt_max);
+                alpha *= p->f_alpha;
+            }
+        } else {
+            npos = 0;
+            nneg++;
+            if (nneg > p->n_neg_max) { status = 2; break; }
+            if (!(p->initial_delay && it < p->n_delay)) {
+                dt = fmax(dt * p->f_dec, p->dt_min);
+                alpha = p->alpha0;
+            }
+            for (int64_t a = 0; a < N * d; ++a) {
+                x[a] -= 0.5 * dt * v[a];
+                v[a] = 0.0;
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            double m = mass ? mass[i] : 1.0;
+            for (int k = 0; k < d; ++k) v[i * d + k] += dt * F[i * d + k] / m;
+        }
+        if (P > 0.0) {
+            double vv = 0.0, ff = 0.0;
+            for (int64_t a = 0; a < N * d; ++a) { vv += v[a] * v[a]; ff += F[a] * F[a]; }
+            double vn = sqrt(vv), fn = sqrt(ff);
+            if (fn > 0.0)
+                for (int64_t a = 0; a < N * d; ++a)
+                    v[a] = (1.0 - alpha) * v[a] + alpha * vn * F[a] / fn;
+        }
+        for (int64_t i = 0; i < N; ++i)
+            for (int k = 0; k < d; ++k) {
+                x[i * d + k] += dt * v[i * d + k];
+                x[i * d + k] = wrap(x[i * d + k], L, img ? &img[i * d + k] : NULL);
+            }
+        if (vl_needs_rebuild(&vl, d, N, L, x, skin)) vl_build(&vl, d, N, L, x, sigma, skin);
+        orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
+        it++;
+    }
+    double fmax2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += F[i * d + k] * F[i * d + k];
+        if (s > fmax2) fmax2 = s;
+    }
+    out[0] = (double)it;
+    out[1] = E;
+    out[2] = sqrt(fmax2);
+    out[3] = (double)vl.builds;
+    vl_free(&vl);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* SWAP Monte Carlo                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Interaction energy of atom a, given the diameter sa, with every atom
+ * except a and b (the swap partner), by brute force over all atoms. */
+static double energy_with(int d, int64_t N, double L, const double *x,
+                          const double *sigma, double eps, int64_t a, double sa,
+                          int64_t b)
+{
+    double e = 0.0, fr;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k == a || k == b) continue;
+        double r = sqrt(dist2(d, L, x, a, k));
+        e += orc_harmonic(r, 0.5 * (sa + sigma[k]), eps, &fr);
+    }
+    return e;
+}
+
+/* One SWAP pass over npairs candidate pairs, serially and in order
+ * (Sec. II.D).  For pair (i, j): E_b (Eq. (10)) and E_a (Eq. (11)) are the
+ * energies of i and j with all other atoms before and after exchanging
+ * their diameters.  Reading: the partner is excluded from both sums (the
+ * i-j term is unchanged by the exchange).  Metropolis: accept iff
+ * u < exp(-(E_a - E_b)/T).  On acceptance sigma and mass are exchanged and
+ * each velocity is rescaled by sqrt(m_old/m_new) so that each atom keeps
+ * its kinetic energy.  accepted[k] (nullable) records each decision.
+ * Returns the number of accepted exchanges. */
+int64_t orc_swap(int d, int64_t N, double L, const double *x, double *sigma,
+                 double *mass, double *v, double eps, double T, int64_t npairs,
+                 const int32_t *pairs, const double *uniforms, int8_t *accepted)
+{
+    int64_t nacc = 0;
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t i = pairs[2 * p], j = pairs[2 * p + 1];
+        int acc = 0;
+        if (i != j) {
+            double Eb = energy_with(d, N, L, x, sigma, eps, i, sigma[i], j)
+                      + energy_with(d, N, L, x, sigma, eps, j, sigma[j], i);
+            double Ea = energy_with(d, N, L, x, sigma, eps, i, sigma[j], j)
+                      + energy_with(d, N, L, x, sigma, eps, j, sigma[i], i);
+            acc = uniforms[p] < exp(-(Ea - Eb) / T);
+        }
+        if (acc) {
+            double t = sigma[i]; sigma[i] = sigma[j]; sigma[j] = t;
+            if (mass) {
+                double mi = mass[i], mj = mass[j];
+                if (v) {
+                    for (int k = 0; k < d; ++k) {
+                        v[i * d + k] *= sqrt(mi / mj);
+                        v[j * d + k] *= sqrt(mj / mi);
+                    }
+                }
+                mass[i] = mj; mass[j] = mi;
+            }
+            ++nacc;
+        }
+        if (accepted) accepted[p] = (int8_t)acc;
+    }
+    return nacc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 and the seeded SWAP draw                               */
+/* ------------------------------------------------------------------ */
+
+/* Philox4x32 with 10 rounds, from its published definition (Salmon, Moraes,
+ * Dror and Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11):
+ * each round multiplies words 0 and 2 by two fixed odd constants, mixes the
+ * high halves with words 1 and 3 and the key, and the key is advanced by
+ * two Weyl increments between rounds. */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Candidate pair p of SWAP pass `sweep` under `seed`: one Philox block at
+ * counter (p, sweep, 0x53574150, 0) and key (seed low, seed high) gives
+ * i = floor(w0 N / 2^32), j' = floor(w1 (N-1) / 2^32), j = j' + (j' >= i)
+ * (so j != i, both uniform), and u = (w2 + 2^32 w3) / 2^64 truncated to
+ * 53 bits, in [0, 1). */
+void orc_swap_draw(uint64_t seed, int64_t sweep, int64_t npairs, int64_t N,
+                   int32_t *pairs, double *uniforms)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t p = 0; p < npairs; ++p) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)sweep, 0x53574150u, 0u}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        int64_t i = (int64_t)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+        int64_t j = (int64_t)(((uint64_t)w[1] * (uint64_t)(N - 1)) >> 32);
+        if (j >= i) ++j;
+        uint64_t bits = ((uint64_t)w[3] << 32) | w[2];
+        pairs[2 * p] = (int32_t)i;
+        pairs[2 * p + 1] = (int32_t)j;
+        uniforms[p] = (double)(bits >> 11) * (1.0 / 9007199254740992.0);
+    }
+}

@@ -1,0 +1,369 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by
+mathematics (closed forms, exact lattice counts, invariants, brute force),
+never against the oracle's own formulas retyped.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from paper_2112_12271_gb300 import workloads as W
+
+
+# ------------------------------------------------------------------ geometry
+def test_sphere_volume_closed_forms(orc):
+    # Eq. (2) against the textbook volumes of balls of radius r = sigma/2
+    r = 0.65
+    s = 2 * r
+    assert orc.sphere_volume(2, s) == pytest.approx(math.pi * r ** 2, rel=1e-14)
+    assert orc.sphere_volume(3, s) == pytest.approx(4.0 / 3.0 * math.pi * r ** 3, rel=1e-14)
+    assert orc.sphere_volume(4, s) == pytest.approx(0.5 * math.pi ** 2 * r ** 4, rel=1e-14)
+    assert orc.sphere_volume(6, s) == pytest.approx(math.pi ** 3 / 6 * r ** 6, rel=1e-14)
+    # the input generator's copy agrees
+    for d in range(2, 11):
+        assert W.sphere_volume(d, s) == pytest.approx(orc.sphere_volume(d, s), rel=1e-14)
+
+
+def test_benchmark_geometry_golden(orc):
+    rows = read_golden("benchmark_geometry.txt")
+    sysd3 = W.c0_bidisperse_d3()
+    assert sysd3.L == pytest.approx(float(rows[0][4]), abs=1e-5)
+    assert orc.n_cell(sysd3.L, 1.4 + 0.3) == int(rows[0][5])
+    sysd6 = W.c1_poly_d6(N=4096)
+    assert orc.n_cell(6.0, sysd6.sigma.max() + 0.3) == int(rows[1][5])
+    # hand check of V_part for the bidisperse system
+    vpart = 500 * math.pi / 6 * (1 + 1.4 ** 3)
+    assert sysd3.L == pytest.approx((vpart / 0.6) ** (1 / 3), rel=1e-12)
+
+
+def test_cell_index_hand_examples(orc):
+    # Eq. (9), axis 1 most significant
+    assert orc.cell_index(2, 3, [0, 0]) == 0
+    assert orc.cell_index(2, 3, [0, 2]) == 2
+    assert orc.cell_index(2, 3, [1, 0]) == 3
+    assert orc.cell_index(2, 3, [2, 2]) == 8
+    assert orc.cell_index(3, 4, [1, 2, 3]) == 27
+    assert orc.n_cell(10.0, 2.5) == 4
+    assert orc.n_cell(9.99, 2.5) == 3
+
+
+def test_min_image(orc):
+    assert orc.min_image(4.0, 10.0) == pytest.approx(4.0)
+    assert orc.min_image(6.0, 10.0) == pytest.approx(-4.0)
+    assert orc.min_image(-6.0, 10.0) == pytest.approx(4.0)
+
+
+# ------------------------------------------------------------------ lists
+@pytest.mark.parametrize("row", read_golden("lattice_neighbor_counts.txt"))
+def test_lattice_counts(orc, row):
+    d, n, rad, expect = int(row[0]), int(row[1]), float(row[2]), int(row[3])
+    x, L = W.lattice(d, n)
+    sigma = np.ones(len(x))
+    skin = rad - 1.0
+    for fn in (orc.neighbors_brute, orc.neighbors_cells):
+        counts, idx = fn(x, sigma, L, skin)
+        assert (counts == expect).all(), (fn.__name__, np.unique(counts))
+
+
+def _random_system(d, N, L, seed):
+    rng = np.random.default_rng(seed)
+    return W.uniform_positions(rng, N, d, L), W.polydisperse(rng, N)
+
+
+@pytest.mark.parametrize("d,N,L", [(2, 400, 14.0), (3, 500, 7.0), (3, 300, 4.6),
+                                   (4, 600, 6.2), (5, 500, 4.6), (6, 700, 4.1),
+                                   (7, 300, 3.2), (8, 300, 3.1), (9, 200, 3.05),
+                                   (10, 200, 3.02)])
+def test_cells_equal_brute(orc, d, N, L):
+    x, sigma = _random_system(d, N, L, seed=d * 7 + N)
+    for gc in (False, True):
+        cb, ib = orc.neighbors_brute(x, sigma, L, 0.3, global_cut=gc)
+        cc, ic = orc.neighbors_cells(x, sigma, L, 0.3, global_cut=gc)
+        assert (cb == cc).all()
+        assert (ib == ic).all()
+        sets = orc.lists_as_sets(cb, ib)
+        for i, s in enumerate(sets):   # j in VL(i) <=> i in VL(j)
+            for j in s:
+                assert i in sets[j]
+    # explicit distance check of a few pairs against the plain definition
+    sets = orc.lists_as_sets(*orc.neighbors_brute(x, sigma, L, 0.3))
+    for i in range(0, N, max(1, N // 7)):
+        for j in range(N):
+            if j == i:
+                continue
+            dx = x[j] - x[i]
+            dx -= L * np.round(dx / L)
+            inside = float(dx @ dx) < (0.5 * (sigma[i] + sigma[j]) + 0.3) ** 2
+            assert inside == (j in sets[i])
+
+
+def test_cells_need_two_subcells(orc):
+    x, sigma = _random_system(3, 50, 2.5, 0)
+    with pytest.raises(ValueError):
+        orc.neighbors_cells(x, sigma, 2.5, 0.3)
+
+
+# ------------------------------------------------------------------ forces
+def test_two_body_closed_form(orc):
+    L = 10.0
+    for (xa, xb, sep) in [(-0.4, 0.4, 0.8), (-4.9, 4.7, 0.4)]:   # second pair wraps
+        x = np.array([[xa, 0.0, 0.0], [xb, 0.0, 0.0]])
+        sig = np.array([1.0, 1.0])
+        F, E, Wv = orc.forces(x, sig, L)
+        g = 1.0 - sep
+        assert E == pytest.approx(0.5 * g * g, rel=1e-13)
+        # |f| = (eps/sigma)(1 - r/sigma), repulsive; virial = r |f|
+        direction = np.sign(orc.min_image(xa - xb, L))
+        assert F[0, 0] == pytest.approx(direction * g, rel=1e-13)
+        assert F[1, 0] == pytest.approx(-direction * g, rel=1e-13)
+        assert Wv == pytest.approx(sep * g, rel=1e-13)
+    # unequal diameters: sigma_ij = 1.2, eps = 2
+    x = np.array([[0.0, 0.0], [0.6, 0.8]])
+    F, E, Wv = orc.forces(x, np.array([1.0, 1.4]), 10.0, eps=2.0)
+    g = 1.0 - 1.0 / 1.2
+    assert E == pytest.approx(0.5 * 2.0 * g * g, rel=1e-13)
+    assert np.linalg.norm(F[0]) == pytest.approx(2.0 / 1.2 * g, rel=1e-13)
+    # touching or apart: nothing
+    F, E, Wv = orc.forces(np.array([[0.0, 0.0], [1.2, 0.0]]), np.array([1.0, 1.4]), 10.0)
+    assert E == 0.0 and not F.any()
+
+
+def _dense(d, N, phi, seed):
+    s = W.make_system(d, N, phi=phi, dist="poly", T=1e-3, seed=seed)
+    return s.x, s.sigma, s.L
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 6])
+def test_force_is_minus_gradient(orc, d):
+    x, sigma, L = _dense(d, 40, 0.5 if d < 5 else 0.25, seed=d)
+    F, E, _ = orc.forces(x, sigma, L)
+    h = 1e-6
+    rng = np.random.default_rng(d)
+    for i in rng.choice(len(x), 8, replace=False):
+        for k in range(d):
+            xp = x.copy(); xp[i, k] += h
+            xm = x.copy(); xm[i, k] -= h
+            fd = -(orc.forces(xp, sigma, L)[1] - orc.forces(xm, sigma, L)[1]) / (2 * h)
+            assert fd == pytest.approx(F[i, k], rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("d", [3, 5, 8])
+def test_newton_third_law_and_list_equals_brute(orc, d):
+    x, sigma, L = _dense(d, 300, 0.45 * W.jamming_estimate(d) / 0.7 + 0.1, seed=11 + d)
+    Fb, Eb, Wb = orc.forces(x, sigma, L)
+    lists = orc.neighbors_cells(x, sigma, L, 0.3) if orc.n_cell(L, sigma.max() + 0.3) >= 2 \
+        else orc.neighbors_brute(x, sigma, L, 0.3)
+    Fl, El, Wl = orc.forces(x, sigma, L, lists=lists)
+    scale = np.abs(Fb).max()
+    assert scale > 0
+    assert np.abs(Fl.sum(axis=0)).max() < 1e-12 * scale * len(x)
+    assert np.abs(Fl - Fb).max() < 1e-13 * scale
+    assert El == pytest.approx(Eb, rel=1e-12)
+    assert Wl == pytest.approx(Wb, rel=1e-12)
+
+
+@pytest.mark.parametrize("d", [3, 6])
+def test_virial_from_volume_scaling(orc, d):
+    # W = sum_{i<j} r_ij . f_ij = -dE/dlambda under x -> lambda x, L -> lambda L
+    x, sigma, L = _dense(d, 60, 0.55 if d == 3 else 0.2, seed=5)
+    _, E0, Wv = orc.forces(x, sigma, L)
+    h = 1e-6
+    Ep = orc.forces(x * (1 + h), sigma, L * (1 + h))[1]
+    Em = orc.forces(x * (1 - h), sigma, L * (1 - h))[1]
+    assert Wv == pytest.approx(-(Ep - Em) / (2 * h), rel=1e-6)
+
+
+def test_translation_invariance(orc):
+    x, sigma, L = _dense(4, 80, 0.4, seed=3)
+    F, E, Wv = orc.forces(x, sigma, L)
+    y = x + np.array([0.37, -1.1, 2.9, 0.05])
+    y = (y + 0.5 * L) % L - 0.5 * L
+    F2, E2, W2 = orc.forces(y, sigma, L)
+    assert E2 == pytest.approx(E, rel=1e-12)
+    assert np.abs(F2 - F).max() < 1e-12 * np.abs(F).max()
+
+
+# ------------------------------------------------------------------ velocity Verlet
+def test_head_on_collision_closed_form(orc):
+    # equal spheres (sigma = m = 1) approach at relative speed 1; in contact
+    # the separation obeys r'' = 2 (1 - r): half a period pi/sqrt(2); then
+    # the velocities are exchanged (elastic, equal masses).
+    L = 10.0
+    x = np.array([[-1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    v = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+    sig = np.ones(2)
+    dt = 0.001
+    t_end = 5.0
+    out = orc.md_steps(x, v, sig, L, int(round(t_end / dt)), dt, skin=0.3)
+    t_exit = 1.0 + math.pi / math.sqrt(2.0)
+    xa = -0.5 - 0.5 * (t_end - t_exit)
+    assert out["x"][0, 0] == pytest.approx(xa, abs=2e-6)
+    assert out["x"][1, 0] == pytest.approx(-xa, abs=2e-6)
+    assert out["v"][0, 0] == pytest.approx(-0.5, abs=2e-6)   # O(dt^2)
+    assert out["v"][1, 0] == pytest.approx(0.5, abs=2e-6)
+
+
+def test_time_reversibility_and_momentum(orc):
+    s = W.make_system(3, 200, phi=0.55, dist="bi", T=1e-2, seed=4)
+    fwd = orc.md_steps(s.x, s.v, s.sigma, s.L, 200, 0.005)
+    assert np.abs(fwd["v"].sum(axis=0)).max() < 1e-12
+    back = orc.md_steps(fwd["x"], -fwd["v"], s.sigma, s.L, 200, 0.005, F=fwd["F"])
+    dx = back["x"] - s.x
+    dx -= s.L * np.round(dx / s.L)
+    assert np.abs(dx).max() < 1e-9
+    assert np.abs(back["v"] + s.v).max() < 1e-9
+    assert fwd["builds"] >= 2      # the trigger fired on the way
+
+
+def test_energy_error_scales_as_dt_squared(orc):
+    s = W.make_system(3, 150, phi=0.60, dist="bi", T=1e-2, seed=8)
+    errs = []
+    for dt in (0.01, 0.005):
+        n = int(round(2.0 / dt))
+        F, E0, _ = orc.forces(s.x, s.sigma, s.L)
+        H0 = E0 + orc.kinetic(s.v)
+        dev, x, v = 0.0, s.x, s.v
+        for _ in range(20):
+            o = orc.md_steps(x, v, s.sigma, s.L, n // 20, dt, F=F)
+            x, v, F = o["x"], o["v"], o["F"]
+            dev = max(dev, abs(o["E"] + o["K"] - H0))
+        errs.append(dev)
+    ratio = errs[0] / errs[1]
+    assert 3.0 < ratio < 5.5, errs
+
+
+# ------------------------------------------------------------------ FIRE
+def test_fire_two_spheres_reach_contact(orc):
+    x = np.array([[0.0, 0.0, 0.0], [0.7, 0.1, 0.0]])
+    sig = np.array([1.0, 1.4])
+    out = orc.fire(x, sig, 10.0)
+    assert out["status"] == 0
+    r = np.linalg.norm(out["x"][1] - out["x"][0])
+    assert r >= 1.2 * (1 - 1e-9)
+    assert out["E"] < 1e-19
+    assert out["fmax"] < 1e-10
+
+
+def test_fire_unjammed_packing_reaches_zero_energy(orc):
+    s = W.make_system(3, 200, phi=0.35, dist="bi", T=0.0, seed=2)
+    E0 = orc.forces(s.x, s.sigma, s.L)[1]
+    out = orc.fire(s.x, s.sigma, s.L)
+    assert out["status"] == 0 and out["fmax"] < 1e-10
+    assert E0 > 1.0 and out["E"] < 1e-18
+
+
+def test_fire_jammed_packing_converges_with_residual_energy(orc):
+    s = W.make_system(3, 128, phi=0.90, dist="bi", T=0.0, seed=1)
+    E0 = orc.forces(s.x, s.sigma, s.L)[1]
+    out = orc.fire(s.x, s.sigma, s.L)
+    assert out["status"] == 0 and out["fmax"] < 1e-10
+    assert 0.0 < out["E"] < E0
+    # independently: forces at the returned positions are below tolerance
+    F, E, _ = orc.forces(out["x"], s.sigma, s.L)
+    assert np.linalg.norm(F, axis=1).max() < 1e-10
+    assert E == pytest.approx(out["E"], rel=1e-9)
+
+
+# ------------------------------------------------------------------ SWAP
+def test_swap_delta_e_equals_total_energy_change(orc):
+    s = W.make_system(3, 120, phi=0.6, dist="bi", T=0.0, seed=9)
+    rng = np.random.default_rng(0)
+    T = 0.05
+    checked = 0
+    for _ in range(40):
+        i, j = rng.choice(s.N, 2, replace=False)
+        if s.sigma[i] == s.sigma[j]:
+            continue
+        E0 = orc.forces(s.x, s.sigma, s.L)[1]
+        sw = s.sigma.copy(); sw[i], sw[j] = sw[j], sw[i]
+        E1 = orc.forces(s.x, sw, s.L)[1]
+        thr = math.exp(-(E1 - E0) / T)
+        if not (1e-6 < thr < 1 - 1e-6):
+            continue
+        for u, expect in ((thr * (1 - 1e-7), True), (thr * (1 + 1e-7), False)):
+            out = orc.swap(s.x, s.sigma, s.L, T, [[i, j]], [u])
+            assert bool(out["accepted"][0]) == expect
+        checked += 1
+    assert checked >= 5
+
+
+def test_swap_equal_diameters_and_infinite_temperature(orc):
+    s = W.make_system(4, 100, phi=0.4, dist="bi", T=0.0, seed=3)
+    rng = np.random.default_rng(1)
+    pairs, u = W.swap_pairs(rng, s.N, 50)
+    out = orc.swap(s.x, np.ones(s.N), s.L, 1e-3, pairs, u)
+    assert out["accepted"].all()
+    out = orc.swap(s.x, s.sigma, s.L, 1e300, pairs, u)
+    assert out["accepted"].all()
+    # the exchanges compose as a product of transpositions
+    sig = s.sigma.copy()
+    for i, j in pairs:
+        sig[i], sig[j] = sig[j], sig[i]
+    assert (out["sigma"] == sig).all()
+
+
+def test_swap_keeps_each_kinetic_energy(orc):
+    s = W.make_system(3, 60, phi=0.5, dist="bi", T=1e-2, seed=5)
+    mass = s.sigma ** 3
+    pairs, u = W.swap_pairs(np.random.default_rng(2), s.N, 40)
+    out = orc.swap(s.x, s.sigma, s.L, 1e300, pairs, u, mass=mass, v=s.v)
+    k0 = 0.5 * mass * (s.v ** 2).sum(axis=1)
+    k1 = 0.5 * out["mass"] * (out["v"] ** 2).sum(axis=1)
+    assert np.allclose(k0, k1, rtol=1e-13)
+    assert (out["mass"] == out["sigma"] ** 3).all()
+
+
+def test_swap_detailed_balance_three_particles(orc):
+    # fixed positions, diameters {a, a, b}: three states (who holds b); the
+    # chain of SWAP passes must visit them with Boltzmann weights.
+    x = np.array([[0.0, 0.0], [0.95, 0.0], [0.3, 0.9]])
+    L = 8.0
+    a, b = 1.0, 1.3
+    T = 0.02
+    E = []
+    for k in range(3):
+        sg = np.full(3, a); sg[k] = b
+        E.append(orc.forces(x, sg, L)[1])
+    E = np.array(E)
+    w = np.exp(-(E - E.min()) / T)
+    p = w / w.sum()
+    assert p.min() > 0.05            # all states matter
+    rng = np.random.default_rng(123)
+    sg = np.array([b, a, a])
+    visits = np.zeros(3)
+    n = 60000
+    pairs, u = W.swap_pairs(rng, 3, n)
+    for blk in range(0, n, 2000):
+        out = orc.swap(x, sg, L, T, pairs[blk:blk + 2000], u[blk:blk + 2000])
+        # count the state after each attempt by replaying the accepted ones
+        cur = sg.copy()
+        for (i, j), acc in zip(pairs[blk:blk + 2000], out["accepted"]):
+            if acc:
+                cur[i], cur[j] = cur[j], cur[i]
+            visits[int(np.argmax(cur))] += 1
+        assert (cur == out["sigma"]).all()
+        sg = out["sigma"]
+    freq = visits / visits.sum()
+    # loose chi-square-like bound for a correlated chain of 6e4 steps
+    assert np.abs(freq - p).max() < 0.02, (freq, p)
+
+
+# ------------------------------------------------------------------ Philox
+@pytest.mark.parametrize("row", read_golden("philox4x32_10_kat.txt"))
+def test_philox_known_answers(orc, row):
+    ctr = [int(v, 16) for v in row[0:4]]
+    key = [int(v, 16) for v in row[4:6]]
+    out = [int(v, 16) for v in row[6:10]]
+    assert orc.philox4x32_10(ctr, key).tolist() == out
+
+
+def test_swap_draw_properties(orc):
+    pairs, u = orc.swap_draw(12345, 3, 20000, 1000)
+    assert (pairs[:, 0] != pairs[:, 1]).all()
+    assert pairs.min() >= 0 and pairs.max() < 1000
+    assert (u >= 0).all() and (u < 1).all()
+    assert abs(u.mean() - 0.5) < 0.01
+    hist = np.bincount(pairs.ravel(), minlength=1000)
+    assert hist.min() > 10
+    p2, u2 = orc.swap_draw(12345, 4, 20000, 1000)
+    assert not (p2 == pairs).all()
