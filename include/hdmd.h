@@ -1,0 +1,197 @@
+/*
+ * hdmd.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * d-dimensional soft-sphere molecular dynamics of Hoy & Interiano-Alberto,
+ * "Efficient d-dimensional molecular dynamics simulations for studies of the
+ * glass-jamming transition" (arXiv:2112.12271).
+ *
+ * What one system holds: N spheres in a periodic hypercube of side L centred
+ * at the origin, 2 <= d <= 10 (Sec. II: all routines work in any d), with
+ * per-sphere diameters sigma_i, masses m_i, positions, velocities, image
+ * counts, the linked-subcell structure (Sec. II.C, Eqs. (7)-(9)) and a full
+ * Verlet list with skin s.  All of it lives in GPU memory owned by the
+ * library.  The compute steps (binning, list build, forces, integration,
+ * FIRE, SWAP) run as CUDA kernels on the stream given at creation.
+ *
+ * Conventions for every call:
+ *   - returns an hdmd_status; never aborts, throws or exits;
+ *   - host arrays are owned by the caller and copied (pinned memory makes
+ *     the copies asynchronous-capable, pageable memory also works);
+ *   - positions and velocities cross the ABI row-major, x[i*d + k], in the
+ *     caller's atom order; the library may reorder atoms internally but
+ *     every output is returned in the caller's order;
+ *   - calls on one system are not thread-safe; distinct systems are
+ *     independent;
+ *   - on failure hdmd_last_error() describes the cause.
+ */
+#ifndef HDMD_H
+#define HDMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdmd_system hdmd_system; /* opaque, library-owned */
+
+typedef enum {
+    HDMD_OK = 0,
+    HDMD_E_INVALID = 1,        /* bad argument (sizes, box too small, NaN input) */
+    HDMD_E_NOMEM = 2,          /* device allocation failed */
+    HDMD_E_NBR_OVERFLOW = 3,   /* list capacity exceeded and could not be grown */
+    HDMD_E_LOST_ATOM = 4,      /* non-finite coordinates or a displacement beyond the skin */
+    HDMD_E_NOT_CONVERGED = 5,  /* FIRE stopped at max_iter or on the P<=0 limit */
+    HDMD_E_CUDA = 6,           /* a CUDA runtime call failed */
+    HDMD_E_TIMEOUT = 7,        /* a bounded device-side wait ran out */
+    HDMD_E_UNSUPPORTED_D = 8   /* d outside 2..10 */
+} hdmd_status;
+
+typedef enum { HDMD_FP64 = 0, HDMD_MIXED = 1 } hdmd_precision;
+
+/* Pair law.  kind 0: harmonic soft spheres
+ *   U(r) = (eps/2) (1 - r/sigma_ij)^2 for r < sigma_ij, 0 beyond,
+ * with the Lorentz mixing rule sigma_ij = (sigma_i + sigma_j)/2 (Sec. II.A;
+ * the paper states the radial law is a user choice, Eq. (1) being its own
+ * example).  skin: the Verlet-list skin s of Sec. II.C (list radius
+ * sigma_ij + s).  Other kinds are rejected with HDMD_E_INVALID. */
+typedef struct {
+    int kind;
+    double eps;
+    double skin;
+} hdmd_potential;
+
+/* Thermodynamic summary (Sec. II.E): pair energy E = sum_{i<j} U_ij, virial
+ * W = sum_{i<j} r_ij . f_ij, kinetic K = sum m v^2 / 2, T = 2K/(d(N-1)),
+ * P = (2K + W)/(d V).  steps/rebuilds count what the call did. */
+typedef struct {
+    double E_pair, virial, K, T, P;
+    int64_t steps, rebuilds;
+} hdmd_thermo;
+
+/* FIRE 2.0 settings (Sec. II.B; constants of the published FIRE 2.0).
+ * f_tol: stop when max_i |F_i| < f_tol.  polish_tol: in HDMD_MIXED systems
+ * the iteration runs with FP32 pair forces until max_i |F_i| < polish_tol,
+ * then continues with FP64 pair forces (0 disables the switch). */
+typedef struct {
+    double dt0, dt_max, dt_min, f_inc, f_dec, alpha0, f_alpha, f_tol, polish_tol;
+    int64_t n_delay, n_neg_max, max_iter;
+    int initial_delay;
+} hdmd_fire_params;
+
+typedef struct {
+    int64_t iterations;        /* FIRE iterations run */
+    int64_t polish_iterations; /* of which with FP64 pair forces */
+    int64_t rebuilds;          /* Verlet-list builds during the call */
+    double E_pair;             /* final pair energy */
+    double fmax;               /* final max_i |F_i| */
+    int converged;             /* 1 if fmax < f_tol */
+} hdmd_fire_result;
+
+typedef struct {
+    int d;
+    int64_t N;
+    double L;
+    int n_cell;                /* subcells per axis, Eq. (7) */
+    int64_t n_cells;           /* n_cell^d */
+    int list_capacity;         /* entries per atom currently allocated */
+    int lanes_per_atom;        /* threads cooperating on one atom's list */
+    int max_list_length;       /* longest list at the last build */
+    int64_t total_list_entries;/* sum of list lengths at the last build */
+    int precision;             /* hdmd_precision */
+    int graphs;                /* 1 if CUDA graphs with conditional nodes are used */
+    int64_t device_bytes;      /* device memory held by the system */
+} hdmd_info;
+
+/* Create a system: d in 2..10 (else HDMD_E_UNSUPPORTED_D), N >= 2 atoms,
+ * box side L, diameters[N] (host, > 0 and finite, copied).  Requires
+ * L >= 2 (max sigma + skin) so that n_cell = floor(L/(max sigma + skin)) >= 2
+ * (Eq. (7)) and minimum images are unique.  prec selects FP64 or mixed
+ * (FP32 pair arithmetic; FP64 positions, velocities and reductions).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
+ * kernel of this system runs.  Positions start at the origin: call
+ * set_state before anything else.  *out receives the handle. */
+hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
+                          const hdmd_potential *pot, hdmd_precision prec,
+                          void *cuda_stream, hdmd_system **out);
+
+/* Load positions x[N*d] (host, row-major, any real values: wrapped into the
+ * box), velocities v[N*d] (nullable: zero) and masses[N] (nullable: all 1,
+ * positive).  Resets image counts to 0 and forces a list rebuild. */
+hdmd_status set_state(hdmd_system *sys, const double *x, const double *v,
+                      const double *masses);
+
+/* Change the diameters (host [N], copied); forces a rebuild. */
+hdmd_status set_diameters(hdmd_system *sys, const double *diameters);
+
+/* Read back positions wrapped into [-L/2, L/2), velocities, image counts
+ * img[N*d] (x + img L is the unwrapped position), forces f[N*d] at the
+ * current positions and diameters[N].  Every output is nullable.
+ * Synchronises the stream. */
+hdmd_status get_state(hdmd_system *sys, double *x, double *v, int32_t *img,
+                      double *f, double *diameters);
+
+/* Build the cell structure and Verlet lists (Sec. II.C).  force != 0
+ * rebuilds unconditionally; force == 0 rebuilds only if the displacement
+ * trigger fires: 2 max_i |x_i - x_i(last build)| > skin.  *rebuilt (nullable)
+ * receives 1 if a build happened. */
+hdmd_status build_neighbors(hdmd_system *sys, int force, int *rebuilt);
+
+/* Test hook: the current full lists in caller order.  counts[N] receives
+ * each list length; idx (nullable; room for sum(counts) entries) receives
+ * the lists back to back, each sorted ascending.  *total (nullable)
+ * receives sum(counts). */
+hdmd_status get_neighbors(hdmd_system *sys, int32_t *counts, int32_t *idx,
+                          int64_t *total);
+
+/* Pair forces, energy and virial at the current positions (Sec. II.B
+ * getforce), rebuilding the lists first if the trigger fires.  energy and
+ * virial (nullable) receive E_pair and W; forces are kept on the device
+ * (get_state reads them). */
+hdmd_status compute_forces(hdmd_system *sys, double *energy, double *virial);
+
+/* nsteps of kick-drift-kick velocity Verlet in NVE (Sec. II.B) with time
+ * step dt, the displacement trigger checked after every drift on the
+ * device and the lists rebuilt there when it fires.  last (nullable)
+ * receives the thermodynamic state after the final step.  On list overflow
+ * the call restores its starting state, grows the lists and runs again. */
+hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last);
+
+/* FIRE 2.0 minimisation (Sec. II.B).  params NULL takes the defaults
+ * (dt0 0.005, dt_max 0.05, dt_min 1e-4, f_inc 1.1, f_dec 0.5, alpha0 0.25,
+ * f_alpha 0.99, f_tol 1e-10, polish_tol 1e-6, n_delay 20, n_neg_max 2000,
+ * max_iter 10^6, initial_delay 1).  Velocities are zeroed on entry and the
+ * minimised positions replace the state.  Returns HDMD_E_NOT_CONVERGED,
+ * with *res filled, when it stops without reaching f_tol. */
+hdmd_status fire_minimize(hdmd_system *sys, const hdmd_fire_params *params,
+                          hdmd_fire_result *res);
+
+/* SWAP Monte Carlo (Sec. II.D): nsweeps passes of round(p N) candidate
+ * exchanges each, at temperature T.  With pairs == NULL the candidates and
+ * the Metropolis uniforms come from Philox4x32-10 keyed by seed (pass s,
+ * pair k at counter (k, s, 0x53574150, 0)); otherwise pairs[2*npairs]
+ * (host, caller order, i != j) and uniforms[npairs] in [0,1) give one pass
+ * explicitly and p, seed and nsweeps are ignored.  The outcome equals
+ * serial execution of the candidates in order.  *accepted (nullable)
+ * receives the number of accepted exchanges; accepted_flags (nullable,
+ * host, npairs bytes) receives each decision of an explicit pass. */
+hdmd_status swap_sweep(hdmd_system *sys, int nsweeps, double T, double p,
+                       uint64_t seed, const int32_t *pairs, const double *uniforms,
+                       int64_t npairs, int64_t *accepted, uint8_t *accepted_flags);
+
+/* Introspection and tuning. lanes_per_atom in {1,2,4,8,16,32} (0 keeps the
+ * current value); use_graphs 0/1 (-1 keeps).  Takes effect at the next
+ * list build, which this call forces. */
+hdmd_status get_info(hdmd_system *sys, hdmd_info *info);
+hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs);
+
+/* Free everything the system holds.  NULL is accepted. */
+hdmd_status destroy_system(hdmd_system *sys);
+
+/* Description of the last failure on sys, or of the last failure of this
+ * thread when sys is NULL.  Never NULL; valid until the next call. */
+const char *hdmd_last_error(const hdmd_system *sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDMD_H */

@@ -1,0 +1,169 @@
+// common.cuh -- device-side data layout shared by the kernels of the hdmd
+// library (d-dimensional soft-sphere MD, arXiv:2112.12271).
+//
+// Layout of one system in GPU memory (atoms in internal, cell-sorted order):
+//   x0, dlt, v, F     FP64 SoA [d][Npad]: the position is x0 + dlt, where x0
+//                     is the position wrapped into the box at the last list
+//                     build and dlt the displacement since then (so the
+//                     rebuild trigger reads |dlt| directly);
+//   sigma, inv_mass   FP64 [Npad] (inv_mass NULL means all masses are 1);
+//   img               int32 SoA [d][Npad] periodic image counts;
+//   id                int32 [Npad] caller index of each internal slot;
+//   gs0               FP32 rows [Npad][RF]: position relative to the centre
+//                     of the atom's subcell at the last build, sigma/2 in
+//                     slot d (read by the list build);
+//   gs[2]             FP32 rows, gs0 + (float)dlt: what the mixed-precision
+//                     force loop gathers (ping-pong between MD steps);
+//   gd[2]             FP64 rows [Npad][RD]: absolute position x0 + dlt and
+//                     sigma/2, gathered by the FP64 force loop;
+//   nbr, code         the full Verlet list: entry m of atom i sits at
+//                     ((m / G) * Npad + i) * G + m % G for G lanes per atom
+//                     (G = 1 is plain padded SoA), code packs for each axis
+//                     the subcell offset o in {-1,0,1} of the neighbour as
+//                     2 bits (o + 1), so x_i - x_j = gs_i - gs_j - o Lsc;
+//   cell_*            counting-sort scratch of the binning.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hdmd {
+
+constexpr int kMaxD = 10;
+constexpr int kNRed = 16;          // reduction slots per block
+
+// reduction slots
+enum Red {
+    R_E = 0,      // sum_i e_i (each pair twice)
+    R_W = 1,      // sum_i w_i (each pair twice)
+    R_K2 = 2,     // sum m v^2
+    R_DMAX2 = 3,  // max |dlt|^2 (max)
+    R_P = 4,      // sum F.v
+    R_VV = 5,     // sum v.v
+    R_VF = 6,     // sum v.F/m
+    R_FF = 7,     // sum (F/m).(F/m)
+    R_FN = 8,     // sum F.F
+    R_FMAX2 = 9,  // max |F_i|^2 (max)
+    R_BAD = 10,   // non-finite seen (max)
+};
+__host__ __device__ constexpr bool red_is_max(int r) { return r == R_DMAX2 || r == R_FMAX2 || r == R_BAD; }
+
+// FIRE scalar state (doubles in Flags::fire)
+enum FireSlot {
+    FS_DT = 0, FS_ALPHA, FS_NPOS, FS_NNEG, FS_ITER, FS_BRANCH, FS_VNORM, FS_FNORM,
+    FS_STATUS, FS_FMAX, FS_E, FS_PHASE_ITER,
+    // parameters
+    FP_DTMAX, FP_DTMIN, FP_FINC, FP_FDEC, FP_ALPHA0, FP_FALPHA, FP_FTOL, FP_SWITCH,
+    FP_NDELAY, FP_NNEGMAX, FP_MAXITER, FP_INITDELAY,
+    FS_COUNT
+};
+enum FireStatus { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_NEGFAIL = 3,
+                  FIRE_SWITCH = 4 };
+
+enum ErrBits { ERR_OVERFLOW = 1, ERR_LOST = 2, ERR_BADARG = 4 };
+
+struct Flags {
+    unsigned int counter;    // last-block-done ticket
+    int rebuild;             // 1: the displacement trigger fired
+    int error;               // ErrBits
+    int max_count;           // longest list seen by the last build
+    int nbuilds;             // builds since creation
+    int pad0;
+    long long total_entries; // sum of list lengths at the last build
+    double fire[FS_COUNT];
+};
+
+struct Dev {
+    int d, N, Npad, G, cap;
+    double L, halfL, invL, skin, eps;
+    int n;          // subcells per axis
+    int ncells;
+    double Lsc, invLsc;
+    float Lsc_f, L_f, halfL_f;
+    double *x0, *dlt, *v, *F, *sigma, *inv_mass;
+    int32_t *img, *id;
+    float *gs0, *gs[2];
+    double *gd[2];
+    // binning scratch (old order copies during a build)
+    int32_t *cell_count, *cell_fill, *cell_start, *cell_of, *perm;
+    int32_t *cellid;        // subcell of each internal slot at the last build
+    double *tx, *tv, *tsig, *tim;
+    int32_t *timg, *tid;
+    // lists
+    int32_t *nnbr, *nbr;
+    uint32_t *code;
+    // reductions
+    double *partials, *red;  // partials: [kNRed][maxblocks]
+    int maxblocks;
+    Flags *flags;
+};
+
+template <int D> struct Rows {
+    static constexpr int RF = (D + 1 + 3) & ~3;   // floats per FP32 row
+    static constexpr int RD = (D + 1 + 1) & ~1;   // doubles per FP64 row
+};
+
+__host__ __device__ inline int pow_int(int b, int e) { int r = 1; for (int k = 0; k < e; ++k) r *= b; return r; }
+
+__device__ __forceinline__ int64_t list_pos(int m, int i, int Npad, int G) {
+    return ((int64_t)(m / G) * Npad + i) * G + (m % G);
+}
+
+// Deterministic grid reduction.  Each block reduces its threads' nslots
+// partial values (sums, or maxima for the red_is_max slots) and stores them
+// at dv.partials[slot * maxblocks + block]; the last block to finish (ticket
+// counter, no waiting) folds all blocks' values in a fixed order into
+// dv.red[slot].  Returns true in every thread of the last block.
+template <int NT>
+__device__ bool block_reduce_and_fold(const Dev &dv, double (&acc)[kNRed], int nslots,
+                                      int maxblocks, double *sh /* [NT/32][kNRed] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = 0; r < nslots; ++r) {
+        double a = acc[r];
+        for (int o = 16; o > 0; o >>= 1) {
+            double b = __shfl_xor_sync(0xffffffffu, a, o);
+            a = red_is_max(r) ? fmax(a, b) : a + b;
+        }
+        if (lane == 0) sh[warp * kNRed + r] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < nslots) {
+        const int r = threadIdx.x;
+        double a = sh[r];
+        for (int w = 1; w < NT / 32; ++w) a = red_is_max(r) ? fmax(a, sh[w * kNRed + r]) : a + sh[w * kNRed + r];
+        dv.partials[(size_t)r * maxblocks + blockIdx.x] = a;
+    }
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(&dv.flags->counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int r = 0; r < nslots; ++r) {
+        double a = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += NT) {
+            double x = __ldcg(dv.partials + (size_t)r * maxblocks + b);
+            a = red_is_max(r) ? fmax(a, x) : a + x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double b = __shfl_xor_sync(0xffffffffu, a, o);
+            a = red_is_max(r) ? fmax(a, b) : a + b;
+        }
+        if (lane == 0) sh[warp * kNRed + r] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < nslots) {
+        const int r = threadIdx.x;
+        double a = sh[r];
+        for (int w = 1; w < NT / 32; ++w) a = red_is_max(r) ? fmax(a, sh[w * kNRed + r]) : a + sh[w * kNRed + r];
+        dv.red[r] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) dv.flags->counter = 0u;
+    return true;
+}
+
+}  // namespace hdmd

@@ -1,0 +1,1274 @@
+// system.cu -- host runtime and C ABI of the hdmd library (include/hdmd.h).
+//
+// Owns the device memory of a system, launches the kernels of the other
+// translation units on the system's stream, and drives the loops of the
+// method: the MD loop (Sec. II.B main loop with the Sec. II.C trigger) and
+// the FIRE loop (Sec. II.B).  Both loops keep every decision on the device:
+// the list rebuild is a CUDA-graph IF node whose condition the drift kernel
+// sets, and the FIRE iteration is a WHILE node whose condition the force
+// kernel sets after its FP64 reductions.  Without conditional-node support
+// the same kernels run eagerly, the rebuild kernels returning at once
+// unless the device-side trigger flag is set.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <cstddef>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hdmd.h"
+#include "launch.h"
+
+using namespace hdmd;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+struct GraphEx {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct hdmd_system {
+    int d = 0;
+    int64_t N = 0;
+    double L = 0;
+    hdmd_potential pot{};
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr, cap_stream3 = nullptr;
+    Dev dv{};
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    bool have_state = false;
+    bool F_valid = false;
+    bool rows32_valid = false, rows64_valid = false;
+    int buf = 0;
+    int use_graphs = 1;
+    bool graphs_ok = true;
+    std::string graph_err;
+    double sigma_max = 0;
+    bool unit_mass = true;
+    double *inv_mass_store = nullptr;
+    double *st_f = nullptr;
+    // list storage (grown on overflow)
+    int32_t *nbr = nullptr;
+    uint32_t *code = nullptr;
+    int64_t list_bytes = 0;
+    // staging
+    double *st_x = nullptr, *st_v = nullptr, *st_m = nullptr, *st_sig = nullptr;
+    int32_t *st_i = nullptr, *st_cnt = nullptr, *st_idx = nullptr;
+    int64_t st_idx_cap = 0;
+    int64_t *st_off = nullptr;
+    // snapshot for md_steps rollback
+    double *snap_x0 = nullptr, *snap_dlt = nullptr, *snap_v = nullptr, *snap_sig = nullptr,
+           *snap_im = nullptr;
+    int32_t *snap_img = nullptr, *snap_id = nullptr;
+    // pinned host mirror of flags and reductions
+    Flags *h_flags = nullptr;
+    double *h_red = nullptr;
+    // graphs
+    std::map<std::tuple<int, int, int, uint64_t>, GraphEx> md_graphs;  // (kind, len, in_buf, dt bits)
+    std::map<int, GraphEx> fire_graphs;                                // fp64 phase -> graph
+    // SWAP buffers (allocated on first use)
+    SwapDev sw{};
+    int sw_cap_pairs = 0;
+    unsigned swap_round = 0;
+    std::string err;
+};
+
+namespace {
+
+hdmd_status fail(hdmd_system *s, hdmd_status code, const std::string &msg) {
+    g_thread_err = msg;
+    if (s) s->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(sys, HDMD_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL(sys)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(sys, HDMD_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+hdmd_status dalloc(hdmd_system *sys, T **p, size_t count) {
+    size_t b = sizeof(T) * (count ? count : 1);
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(sys, HDMD_E_NOMEM, std::string("cudaMalloc of ") + std::to_string(b) +
+                                           " bytes failed: " + cudaGetErrorString(e));
+    }
+    sys->allocs.push_back(q);
+    sys->bytes += (int64_t)b;
+    *p = (T *)q;
+    return HDMD_OK;
+}
+
+#define DA(ptr, count)                                         \
+    do {                                                       \
+        hdmd_status st_ = dalloc(sys, &(ptr), (size_t)(count)); \
+        if (st_ != HDMD_OK) return st_;                        \
+    } while (0)
+
+void free_graphs(hdmd_system *sys) {
+    for (auto &kv : sys->md_graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    sys->md_graphs.clear();
+    for (auto &kv : sys->fire_graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    sys->fire_graphs.clear();
+}
+
+int default_lanes(int64_t N) {
+    if (N <= (1 << 17)) return 4;
+    if (N <= (1 << 20)) return 2;
+    return 1;
+}
+
+// expected longest list: atoms within max sigma + skin at the mean density,
+// with head-room; the build reports the true maximum and the list grows.
+int initial_capacity(const hdmd_system *sys) {
+    const int d = sys->d;
+    const double rho = (double)sys->N / std::pow(sys->L, d);
+    const double R = sys->sigma_max + sys->pot.skin;
+    const double vball = std::pow(M_PI, 0.5 * d) * std::pow(R, d) / std::tgamma(1.0 + 0.5 * d);
+    double est = 1.6 * rho * vball + 16.0;
+    est = std::min(est, (double)sys->N + 8.0);
+    return (int)est;
+}
+
+hdmd_status alloc_lists(hdmd_system *sys, int cap) {
+    const int G = sys->dv.G;
+    cap = ((cap + G - 1) / G) * G;
+    if (cap < G) cap = G;
+    if (sys->nbr) { cudaFree(sys->nbr); sys->nbr = nullptr; }
+    if (sys->code) { cudaFree(sys->code); sys->code = nullptr; }
+    sys->bytes -= sys->list_bytes;
+    const size_t cnt = (size_t)cap * sys->dv.Npad;
+    void *a = nullptr, *b = nullptr;
+    cudaError_t e1 = cudaMalloc(&a, cnt * sizeof(int32_t));
+    cudaError_t e2 = e1 == cudaSuccess ? cudaMalloc(&b, cnt * sizeof(uint32_t)) : e1;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        if (a) cudaFree(a);
+        sys->list_bytes = 0;
+        return fail(sys, HDMD_E_NOMEM, "Verlet list allocation of " +
+                                           std::to_string(2 * cnt * 4) + " bytes failed");
+    }
+    sys->nbr = (int32_t *)a;
+    sys->code = (uint32_t *)b;
+    sys->list_bytes = (int64_t)(2 * cnt * 4);
+    sys->bytes += sys->list_bytes;
+    sys->dv.nbr = sys->nbr;
+    sys->dv.code = sys->code;
+    sys->dv.cap = cap;
+    free_graphs(sys);   // baked pointers changed
+    return HDMD_OK;
+}
+
+hdmd_status read_flags(hdmd_system *sys) {
+    CK(cudaMemcpyAsync(sys->h_flags, sys->dv.flags, sizeof(Flags), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaMemcpyAsync(sys->h_red, sys->dv.red, sizeof(double) * kNRed, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    return HDMD_OK;
+}
+
+hdmd_status clear_flag_field(hdmd_system *sys, size_t offset, size_t bytes) {
+    CK(cudaMemsetAsync((char *)sys->dv.flags + offset, 0, bytes, sys->stream));
+    return HDMD_OK;
+}
+
+hdmd_status clear_errors(hdmd_system *sys) {
+    hdmd_status st = clear_flag_field(sys, offsetof(Flags, error), sizeof(int) * 2);  // error, max_count
+    if (st) return st;
+    return clear_flag_field(sys, offsetof(Flags, rebuild), sizeof(int));
+}
+
+// unconditional list build; rows of buffer `buf` refreshed
+hdmd_status rebuild_now(hdmd_system *sys, int buf) {
+    launch_rebuild(sys->dv, buf, false, sys->stream);
+    CKL(sys);
+    sys->buf = buf;
+    sys->rows32_valid = sys->rows64_valid = true;
+    sys->F_valid = false;
+    return HDMD_OK;
+}
+
+hdmd_status ensure_rows(hdmd_system *sys, int buf, bool need32, bool need64) {
+    bool w32 = need32 && (!sys->rows32_valid || sys->buf != buf);
+    bool w64 = need64 && (!sys->rows64_valid || sys->buf != buf);
+    if (sys->buf != buf) {
+        // the other kind is stale in the new buffer
+        if (!need32) sys->rows32_valid = false;
+        if (!need64) sys->rows64_valid = false;
+    }
+    if (w32 || w64) {
+        launch_rows(sys->dv, buf, w32, w64, sys->stream);
+        CKL(sys);
+    }
+    sys->buf = buf;
+    if (need32) sys->rows32_valid = true;
+    if (need64) sys->rows64_valid = true;
+    return HDMD_OK;
+}
+
+hdmd_status check_device_errors(hdmd_system *sys) {
+    if (sys->h_flags->error & ERR_LOST)
+        return fail(sys, HDMD_E_LOST_ATOM,
+                    "non-finite coordinates or a displacement beyond L/4 since the last list build");
+    if (sys->h_flags->error & ERR_OVERFLOW)
+        return fail(sys, HDMD_E_NBR_OVERFLOW, "Verlet list capacity exceeded");
+    return HDMD_OK;
+}
+
+// grow the lists after an overflow seen by the last build(s)
+hdmd_status grow_lists(hdmd_system *sys) {
+    int need = sys->h_flags->max_count;
+    int cap = (int)(need * 1.25) + 16;
+    if (cap <= sys->dv.cap) cap = sys->dv.cap * 2;
+    return alloc_lists(sys, cap);
+}
+
+hdmd_status build_forced(hdmd_system *sys, int buf) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        hdmd_status st = clear_errors(sys);
+        if (st) return st;
+        st = rebuild_now(sys, buf);
+        if (st) return st;
+        st = read_flags(sys);
+        if (st) return st;
+        if (sys->h_flags->error & ERR_OVERFLOW) {
+            st = grow_lists(sys);
+            if (st) return st;
+            continue;
+        }
+        return HDMD_OK;
+    }
+    return fail(sys, HDMD_E_NBR_OVERFLOW, "Verlet list kept overflowing after growing it");
+}
+
+// ----------------------------------------------------------------- graphs
+// Conditional IF node on the capturing stream, body = a full list build.
+hdmd_status add_if_rebuild(hdmd_system *sys, cudaStream_t cs, cudaGraphConditionalHandle h,
+                           int buf, cudaStream_t body_stream) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    launch_rebuild(sys->dv, buf, false, body_stream);
+    cudaGraph_t out = nullptr;
+    CK(cudaStreamEndCapture(body_stream, &out));
+    return HDMD_OK;
+}
+
+StepCfg base_cfg(const hdmd_system *sys, double dt) {
+    StepCfg c;
+    std::memset(&c, 0, sizeof(c));
+    c.dt = dt;
+    c.halfdt = 0.5 * dt;
+    c.fp64_pairs = sys->prec == HDMD_FP64 ? 1 : 0;
+    return c;
+}
+
+// kind 0: kick-drift from stored F, then IF rebuild (start of md_steps)
+// kind 1: len x [force + kick + kick + drift, IF rebuild]
+hdmd_status build_md_graph(hdmd_system *sys, int kind, int len, int in_buf, double dt,
+                           GraphEx *out) {
+    cudaStream_t cs = sys->cap_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    hdmd_status st = HDMD_OK;
+    int cur = in_buf;
+    const int steps = kind == 0 ? 1 : len;
+    for (int k = 0; k < steps && e == cudaSuccess && st == HDMD_OK; ++k) {
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+        StepCfg c = base_cfg(sys, dt);
+        c.compute_force = kind == 0 ? 0 : 1;
+        c.kick2 = kind == 0 ? 0 : 1;
+        c.kick1_drift = 1;
+        c.in_buf = cur;
+        c.out_buf = 1 - cur;
+        c.cond_rebuild = h;
+        launch_step(sys->dv, c, cs);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        st = add_if_rebuild(sys, cs, h, 1 - cur, sys->cap_stream2);
+        cur = 1 - cur;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (st != HDMD_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(sys, HDMD_E_CUDA, std::string("graph capture: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(sys, HDMD_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    out->graph = graph;
+    out->exec = ex;
+    return HDMD_OK;
+}
+
+uint64_t dbits(double x) { uint64_t b; std::memcpy(&b, &x, 8); return b; }
+
+hdmd_status run_md_piece(hdmd_system *sys, int kind, int len, int in_buf, double dt) {
+    if (sys->use_graphs && sys->graphs_ok) {
+        auto key = std::make_tuple(kind, len, in_buf, dbits(dt));
+        auto it = sys->md_graphs.find(key);
+        if (it == sys->md_graphs.end()) {
+            GraphEx ge;
+            hdmd_status st = build_md_graph(sys, kind, len, in_buf, dt, &ge);
+            if (st != HDMD_OK) {
+                sys->graphs_ok = false;   // fall back to eager launches from now on
+                sys->graph_err = sys->err;
+                g_thread_err.clear();
+                sys->err.clear();
+            } else {
+                it = sys->md_graphs.emplace(key, ge).first;
+            }
+        }
+        if (sys->graphs_ok) {
+            CK(cudaGraphLaunch(it->second.exec, sys->stream));
+            return HDMD_OK;
+        }
+    }
+    // eager: the rebuild kernels check the device-side trigger themselves
+    int cur = in_buf;
+    const int steps = kind == 0 ? 1 : len;
+    for (int k = 0; k < steps; ++k) {
+        StepCfg c = base_cfg(sys, dt);
+        c.compute_force = kind == 0 ? 0 : 1;
+        c.kick2 = kind == 0 ? 0 : 1;
+        c.kick1_drift = 1;
+        c.in_buf = cur;
+        c.out_buf = 1 - cur;
+        launch_step(sys->dv, c, sys->stream);
+        launch_rebuild(sys->dv, 1 - cur, true, sys->stream);
+        CKL(sys);
+        cur = 1 - cur;
+    }
+    return HDMD_OK;
+}
+
+hdmd_status force_only(hdmd_system *sys, int buf, bool fp64, bool thermo) {
+    StepCfg c = base_cfg(sys, 0.0);
+    c.fp64_pairs = fp64 ? 1 : 0;
+    c.compute_force = 1;
+    c.store_F = 1;
+    c.thermo = thermo ? 1 : 0;
+    c.in_buf = buf;
+    c.out_buf = buf;
+    launch_step(sys->dv, c, sys->stream);
+    CKL(sys);
+    return HDMD_OK;
+}
+
+void fill_thermo(const hdmd_system *sys, const double *red, hdmd_thermo *t) {
+    const double K = 0.5 * red[R_K2];
+    const double W = 0.5 * red[R_W];
+    t->E_pair = 0.5 * red[R_E];
+    t->virial = W;
+    t->K = K;
+    t->T = 2.0 * K / (sys->d * (double)(sys->N - 1));
+    t->P = (2.0 * K + W) / (sys->d * std::pow(sys->L, sys->d));
+}
+
+hdmd_status snapshot(hdmd_system *sys, bool restore) {
+    const size_t nd = (size_t)sys->d * sys->dv.Npad, n = sys->dv.Npad;
+    auto cp = [&](void *dst, const void *src, size_t b) {
+        return cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, sys->stream);
+    };
+    Dev &dv = sys->dv;
+    if (!restore) {
+        CK(cp(sys->snap_x0, dv.x0, nd * 8));
+        CK(cp(sys->snap_dlt, dv.dlt, nd * 8));
+        CK(cp(sys->snap_v, dv.v, nd * 8));
+        CK(cp(sys->snap_img, dv.img, nd * 4));
+        CK(cp(sys->snap_id, dv.id, n * 4));
+        CK(cp(sys->snap_sig, dv.sigma, n * 8));
+        if (dv.inv_mass) CK(cp(sys->snap_im, dv.inv_mass, n * 8));
+    } else {
+        CK(cp(dv.x0, sys->snap_x0, nd * 8));
+        CK(cp(dv.dlt, sys->snap_dlt, nd * 8));
+        CK(cp(dv.v, sys->snap_v, nd * 8));
+        CK(cp(dv.img, sys->snap_img, nd * 4));
+        CK(cp(dv.id, sys->snap_id, n * 4));
+        CK(cp(dv.sigma, sys->snap_sig, n * 8));
+        if (dv.inv_mass) CK(cp(dv.inv_mass, sys->snap_im, n * 8));
+    }
+    return HDMD_OK;
+}
+
+constexpr int kChunk = 64;
+
+hdmd_status md_once(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
+    hdmd_status st = clear_errors(sys);
+    if (st) return st;
+    int nb0;
+    CK(cudaMemcpyAsync(&sys->h_flags->nbuilds, &sys->dv.flags->nbuilds, sizeof(int),
+                       cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    nb0 = sys->h_flags->nbuilds;
+    const bool fp64 = sys->prec == HDMD_FP64;
+    st = ensure_rows(sys, sys->buf, !fp64, fp64);
+    if (st) return st;
+    if (!sys->F_valid) {
+        st = force_only(sys, sys->buf, fp64, false);
+        if (st) return st;
+        sys->F_valid = true;
+    }
+    int cur = sys->buf;
+    if (nsteps > 0) {
+        st = run_md_piece(sys, 0, 1, cur, dt);
+        if (st) return st;
+        cur = 1 - cur;
+        int64_t left = nsteps - 1;
+        while (left > 0) {
+            int len = (int)std::min<int64_t>(left, kChunk);
+            st = run_md_piece(sys, 1, len, cur, dt);
+            if (st) return st;
+            if (len & 1) cur = 1 - cur;
+            left -= len;
+        }
+    }
+    // final force, second half kick, thermo
+    StepCfg c = base_cfg(sys, dt);
+    c.compute_force = 1;
+    c.kick2 = nsteps > 0 ? 1 : 0;
+    c.store_F = 1;
+    c.thermo = 1;
+    c.in_buf = cur;
+    c.out_buf = cur;
+    launch_step(sys->dv, c, sys->stream);
+    CKL(sys);
+    sys->buf = cur;
+    if (fp64) { sys->rows64_valid = true; sys->rows32_valid = false; }
+    else { sys->rows32_valid = true; sys->rows64_valid = false; }
+    sys->F_valid = true;
+    st = read_flags(sys);
+    if (st) return st;
+    if (last) {
+        fill_thermo(sys, sys->h_red, last);
+        last->steps = nsteps;
+        last->rebuilds = sys->h_flags->nbuilds - nb0;
+    }
+    return check_device_errors(sys);
+}
+
+
+// ----------------------------------------------------------------- FIRE
+StepCfg fire_force_cfg(const hdmd_system *sys, bool fp64, unsigned long long cond_loop) {
+    StepCfg c = base_cfg(sys, 0.0);
+    c.fp64_pairs = fp64 ? 1 : 0;
+    c.compute_force = 1;
+    c.store_F = 1;
+    c.fire_red = 1;
+    c.in_buf = 0;
+    c.out_buf = 0;
+    c.cond_loop = cond_loop;
+    return c;
+}
+
+// [force + FIRE scalars] then WHILE(running) { update; IF(trigger) build; force + scalars }
+hdmd_status build_fire_graph(hdmd_system *sys, bool fp64, GraphEx *out) {
+    cudaStream_t cs = sys->cap_stream, cs2 = sys->cap_stream2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    hdmd_status st = HDMD_OK;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    cudaGraphConditionalHandle hw = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        launch_step(sys->dv, fire_force_cfg(sys, fp64, hw), cs);
+        e = cudaGetLastError();
+    }
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd);
+    cudaGraphNode_t node;
+    cudaGraphNodeParams p = {};
+    if (e == cudaSuccess) {
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = hw;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        cudaGraphConditionalHandle hi = 0;
+        e = cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            launch_fire_update(sys->dv, fp64 ? 1 : 0, hi, cs2);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) st = add_if_rebuild(sys, cs2, hi, 0, sys->cap_stream3);
+            if (e == cudaSuccess && st == HDMD_OK) {
+                launch_step(sys->dv, fire_force_cfg(sys, fp64, hw), cs2);
+                e = cudaGetLastError();
+            }
+            cudaGraph_t bo = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(cs2, &bo);
+            if (e == cudaSuccess) e = e3;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (st != HDMD_OK || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (st != HDMD_OK) return st;
+        return fail(sys, HDMD_E_CUDA, std::string("FIRE graph capture: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(sys, HDMD_E_CUDA, std::string("FIRE graph instantiate: ") + cudaGetErrorString(e));
+    }
+    out->graph = graph;
+    out->exec = ex;
+    return HDMD_OK;
+}
+
+hdmd_status read_fire(hdmd_system *sys) {
+    CK(cudaMemcpyAsync(sys->h_flags, sys->dv.flags, sizeof(Flags), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    return HDMD_OK;
+}
+
+// one FIRE phase with FP32 or FP64 pair forces, until the status leaves RUNNING
+hdmd_status fire_phase(hdmd_system *sys, bool fp64) {
+    if (sys->use_graphs && sys->graphs_ok) {
+        auto it = sys->fire_graphs.find(fp64 ? 1 : 0);
+        if (it == sys->fire_graphs.end()) {
+            GraphEx ge;
+            hdmd_status st = build_fire_graph(sys, fp64, &ge);
+            if (st != HDMD_OK) {
+                sys->graphs_ok = false;
+                sys->graph_err = sys->err;
+                g_thread_err.clear();
+                sys->err.clear();
+            } else {
+                it = sys->fire_graphs.emplace(fp64 ? 1 : 0, ge).first;
+            }
+        }
+        if (sys->graphs_ok) {
+            CK(cudaGraphLaunch(it->second.exec, sys->stream));
+            return read_fire(sys);
+        }
+    }
+    // eager: fixed bursts of iterations, every kernel returning at once after the end
+    launch_step(sys->dv, fire_force_cfg(sys, fp64, 0), sys->stream);
+    CKL(sys);
+    for (;;) {
+        for (int k = 0; k < 32; ++k) {
+            launch_fire_update(sys->dv, fp64 ? 1 : 0, 0, sys->stream);
+            launch_rebuild(sys->dv, 0, true, sys->stream);
+            launch_step(sys->dv, fire_force_cfg(sys, fp64, 0), sys->stream);
+        }
+        CKL(sys);
+        hdmd_status st = read_fire(sys);
+        if (st) return st;
+        if (sys->h_flags->fire[FS_STATUS] != (double)FIRE_RUNNING) return HDMD_OK;
+    }
+}
+
+hdmd_status fire_once(hdmd_system *sys, const hdmd_fire_params &p, hdmd_fire_result *res) {
+    Dev &dv = sys->dv;
+    hdmd_status st = clear_errors(sys);
+    if (st) return st;
+    CK(cudaMemsetAsync(dv.v, 0, sizeof(double) * sys->d * dv.Npad, sys->stream));
+    const bool mixed = sys->prec == HDMD_MIXED;
+    double fs[FS_COUNT] = {0};
+    fs[FS_DT] = p.dt0;
+    fs[FS_ALPHA] = p.alpha0;
+    fs[FS_STATUS] = FIRE_RUNNING;
+    fs[FP_DTMAX] = p.dt_max;
+    fs[FP_DTMIN] = p.dt_min;
+    fs[FP_FINC] = p.f_inc;
+    fs[FP_FDEC] = p.f_dec;
+    fs[FP_ALPHA0] = p.alpha0;
+    fs[FP_FALPHA] = p.f_alpha;
+    fs[FP_FTOL] = p.f_tol;
+    fs[FP_SWITCH] = (mixed && p.polish_tol > p.f_tol) ? p.polish_tol : 0.0;
+    fs[FP_NDELAY] = (double)p.n_delay;
+    fs[FP_NNEGMAX] = (double)p.n_neg_max;
+    fs[FP_MAXITER] = (double)p.max_iter;
+    fs[FP_INITDELAY] = p.initial_delay ? 1.0 : 0.0;
+    std::memcpy(sys->h_flags->fire, fs, sizeof(fs));
+    CK(cudaMemcpyAsync(dv.flags->fire, sys->h_flags->fire, sizeof(fs), cudaMemcpyHostToDevice, sys->stream));
+    CK(cudaMemcpyAsync(&sys->h_flags->nbuilds, &dv.flags->nbuilds, sizeof(int), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    const int nb0 = sys->h_flags->nbuilds;
+    bool fp64 = !mixed;
+    st = ensure_rows(sys, 0, true, fp64);
+    if (st) return st;
+    st = fire_phase(sys, fp64);
+    if (st) return st;
+    int64_t polish = 0;
+    if (sys->h_flags->fire[FS_STATUS] == (double)FIRE_SWITCH && !(sys->h_flags->error & (ERR_LOST | ERR_OVERFLOW))) {
+        // continue the same FIRE iteration with FP64 pair forces
+        sys->h_flags->fire[FP_SWITCH] = 0.0;
+        sys->h_flags->fire[FS_STATUS] = FIRE_RUNNING;
+        sys->h_flags->fire[FS_PHASE_ITER] = 0.0;
+        CK(cudaMemcpyAsync(dv.flags->fire, sys->h_flags->fire, sizeof(double) * FS_COUNT,
+                           cudaMemcpyHostToDevice, sys->stream));
+        sys->rows64_valid = false;
+        st = ensure_rows(sys, 0, true, true);
+        if (st) return st;
+        fp64 = true;
+        st = fire_phase(sys, true);
+        if (st) return st;
+        polish = (int64_t)sys->h_flags->fire[FS_PHASE_ITER];
+    }
+    sys->buf = 0;
+    sys->rows32_valid = true;
+    sys->rows64_valid = fp64;
+    sys->F_valid = true;
+    const double *f = sys->h_flags->fire;
+    if (res) {
+        res->iterations = (int64_t)f[FS_ITER];
+        res->polish_iterations = polish;
+        res->rebuilds = sys->h_flags->nbuilds - nb0;
+        res->E_pair = f[FS_E];
+        res->fmax = f[FS_FMAX];
+        res->converged = f[FS_STATUS] == (double)FIRE_CONVERGED;
+    }
+    st = check_device_errors(sys);
+    if (st) return st;
+    if (f[FS_STATUS] != (double)FIRE_CONVERGED) {
+        const int s = (int)f[FS_STATUS];
+        return fail(sys, HDMD_E_NOT_CONVERGED,
+                    s == FIRE_MAXITER ? "FIRE reached max_iter" : "FIRE stopped: too many P <= 0 steps or non-finite forces");
+    }
+    return HDMD_OK;
+}
+
+
+// ----------------------------------------------------------------- SWAP
+hdmd_status swap_alloc(hdmd_system *sys, int npairs, int scap) {
+    SwapDev &sw = sys->sw;
+    if (npairs <= sys->sw_cap_pairs && scap <= sw.scap) return HDMD_OK;
+    auto rel = [](void *p) { if (p) cudaFree(p); };
+    if (npairs > sys->sw_cap_pairs) {
+        rel(sw.ids); rel(sw.u); rel(sw.pairs); rel(sw.state); rel(sw.scount);
+        sw.ids = nullptr; sw.u = nullptr; sw.pairs = nullptr; sw.state = nullptr; sw.scount = nullptr;
+        if (cudaMalloc((void **)&sw.ids, sizeof(int32_t) * 2 * npairs) != cudaSuccess ||
+            cudaMalloc((void **)&sw.u, sizeof(double) * npairs) != cudaSuccess ||
+            cudaMalloc((void **)&sw.pairs, sizeof(int32_t) * 2 * npairs) != cudaSuccess ||
+            cudaMalloc((void **)&sw.state, npairs) != cudaSuccess ||
+            cudaMalloc((void **)&sw.scount, sizeof(int32_t) * 2 * npairs) != cudaSuccess) {
+            cudaGetLastError();
+            sys->sw_cap_pairs = 0;
+            return fail(sys, HDMD_E_NOMEM, "SWAP pair buffers");
+        }
+        sys->sw_cap_pairs = npairs;
+        rel(sw.slist);
+        sw.slist = nullptr;
+        sw.scap = 0;
+    }
+    if (!sw.owner) {
+        if (cudaMalloc((void **)&sw.owner, sizeof(unsigned long long) * sys->dv.Npad) != cudaSuccess ||
+            cudaMalloc((void **)&sw.slot_of, sizeof(int32_t) * sys->dv.Npad) != cudaSuccess ||
+            cudaMalloc((void **)&sw.overflow, sizeof(int) * 4) != cudaSuccess ||
+            cudaMalloc((void **)&sw.nacc, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(sys, HDMD_E_NOMEM, "SWAP owner buffers");
+        }
+        sw.npend = sw.overflow + 1;
+        CK(cudaMemsetAsync(sw.owner, 0xFF, sizeof(unsigned long long) * sys->dv.Npad, sys->stream));
+    }
+    if (scap > sw.scap || !sw.slist) {
+        rel(sw.slist);
+        sw.slist = nullptr;
+        if (cudaMalloc((void **)&sw.slist, sizeof(int32_t) * (size_t)2 * sys->sw_cap_pairs * scap) != cudaSuccess) {
+            cudaGetLastError();
+            sw.scap = 0;
+            return fail(sys, HDMD_E_NOMEM, "SWAP neighbour lists");
+        }
+        sw.scap = scap;
+    }
+    return HDMD_OK;
+}
+
+void swap_free(hdmd_system *sys) {
+    SwapDev &sw = sys->sw;
+    for (void *p : {(void *)sw.ids, (void *)sw.u, (void *)sw.pairs, (void *)sw.state, (void *)sw.owner,
+                    (void *)sw.slot_of, (void *)sw.slist, (void *)sw.scount, (void *)sw.overflow,
+                    (void *)sw.nacc})
+        if (p) cudaFree(p);
+    sw = SwapDev{};
+}
+
+int swap_list_estimate(const hdmd_system *sys) {
+    const int d = sys->d;
+    const double rho = (double)sys->N / std::pow(sys->L, d);
+    const double R = sys->sigma_max;
+    const double vball = std::pow(M_PI, 0.5 * d) * std::pow(R, d) / std::tgamma(1.0 + 0.5 * d);
+    return (int)std::min(2.0 * rho * vball + 32.0, (double)sys->N + 1.0);
+}
+
+// one pass over the candidates already in sw.ids / sw.u
+hdmd_status swap_pass(hdmd_system *sys) {
+    SwapDev &sw = sys->sw;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        CK(cudaMemsetAsync(sw.overflow, 0, sizeof(int), sys->stream));
+        launch_swap_prepare(sys->dv, sw, sys->buf, sys->stream);
+        CKL(sys);
+        int ov = 0;
+        CK(cudaMemcpyAsync(&sys->h_flags->pad0, sw.overflow, sizeof(int), cudaMemcpyDeviceToHost, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+        ov = sys->h_flags->pad0;
+        if (ov == 0) break;
+        hdmd_status st = swap_alloc(sys, sys->sw_cap_pairs, (int)(ov * 1.25) + 16);
+        if (st) return st;
+        if (attempt == 5) return fail(sys, HDMD_E_NBR_OVERFLOW, "SWAP neighbour lists kept overflowing");
+    }
+    const int64_t max_rounds = (int64_t)sw.npairs + 2;
+    int64_t done_rounds = 0;
+    for (;;) {
+        const int burst = 8;
+        for (int r = 0; r < burst; ++r) {
+            if (r == burst - 1) CK(cudaMemsetAsync(sw.npend, 0, sizeof(int), sys->stream));
+            launch_swap_round(sys->dv, sw, sys->swap_round++, sys->stream);
+        }
+        CKL(sys);
+        done_rounds += burst;
+        CK(cudaMemcpyAsync(&sys->h_flags->pad0, sw.npend, sizeof(int), cudaMemcpyDeviceToHost, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+        if (sys->h_flags->pad0 == 0) return HDMD_OK;
+        if (done_rounds > max_rounds + burst)
+            return fail(sys, HDMD_E_TIMEOUT, "SWAP rounds did not finish");
+    }
+}
+
+hdmd_status validate_sys(hdmd_system *sys) {
+    if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
+    if (!sys->have_state) return fail(sys, HDMD_E_INVALID, "set_state must be called first");
+    return HDMD_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
+                          const hdmd_potential *pot, hdmd_precision prec, void *cuda_stream,
+                          hdmd_system **out) {
+    hdmd_system *sys = nullptr;
+    if (!out) return fail(nullptr, HDMD_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (d < 2 || d > kMaxD) return fail(nullptr, HDMD_E_UNSUPPORTED_D, "d must be in 2..10");
+    if (N < 2 || N > (int64_t)1 << 28) return fail(nullptr, HDMD_E_INVALID, "N must be in 2..2^28");
+    if (!(L > 0.0) || !std::isfinite(L)) return fail(nullptr, HDMD_E_INVALID, "L must be positive and finite");
+    if (!diameters) return fail(nullptr, HDMD_E_INVALID, "diameters is NULL");
+    if (!pot) return fail(nullptr, HDMD_E_INVALID, "potential is NULL");
+    if (pot->kind != 0) return fail(nullptr, HDMD_E_INVALID, "only the harmonic pair law (kind 0) is available");
+    if (!(pot->eps > 0.0) || !std::isfinite(pot->eps)) return fail(nullptr, HDMD_E_INVALID, "eps must be positive");
+    if (!(pot->skin >= 0.0) || !std::isfinite(pot->skin)) return fail(nullptr, HDMD_E_INVALID, "skin must be >= 0");
+    if (prec != HDMD_FP64 && prec != HDMD_MIXED) return fail(nullptr, HDMD_E_INVALID, "unknown precision");
+    double smax = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!(diameters[i] > 0.0) || !std::isfinite(diameters[i]))
+            return fail(nullptr, HDMD_E_INVALID, "diameters must be positive and finite");
+        smax = std::max(smax, diameters[i]);
+    }
+    const double rc = smax + pot->skin;
+    int n = (int)std::floor(L / rc);   // Eq. (7)
+    if (n < 2)
+        return fail(nullptr, HDMD_E_INVALID,
+                    "box too small: L must be >= 2 (max diameter + skin) so that n_cell >= 2");
+    // larger subcells stay exact; cap the subcell count at ~8N (+4096)
+    const double cap_cells = 8.0 * (double)N + 4096.0;
+    while (n > 2 && std::pow((double)n, d) > cap_cells) --n;
+    if (std::pow((double)n, d) > 2.0e9) return fail(nullptr, HDMD_E_INVALID, "too many subcells");
+
+    sys = new hdmd_system();
+    sys->d = d;
+    sys->N = N;
+    sys->L = L;
+    sys->pot = *pot;
+    sys->prec = prec;
+    sys->stream = (cudaStream_t)cuda_stream;
+    sys->sigma_max = smax;
+    Dev &dv = sys->dv;
+    dv.d = d;
+    dv.N = (int)N;
+    dv.Npad = (int)((N + 63) / 64 * 64);
+    dv.G = default_lanes(N);
+    dv.L = L;
+    dv.halfL = 0.5 * L;
+    dv.invL = 1.0 / L;
+    dv.skin = pot->skin;
+    dv.eps = pot->eps;
+    dv.n = n;
+    dv.ncells = 1;
+    for (int k = 0; k < d; ++k) dv.ncells *= n;
+    dv.Lsc = L / n;
+    dv.invLsc = n / L;
+    dv.Lsc_f = (float)dv.Lsc;
+    dv.L_f = (float)L;
+    dv.halfL_f = (float)(0.5 * L);
+
+    auto bail = [&](hdmd_status st) {
+        destroy_system(sys);
+        return st;
+    };
+    const size_t Np = dv.Npad, nd = (size_t)d * Np;
+    const int RF = kRowFloats(d), RD = kRowDoubles(d);
+    hdmd_status st;
+#define DA2(ptr, count) do { st = dalloc(sys, &(ptr), (size_t)(count)); if (st) return bail(st); } while (0)
+    DA2(dv.x0, nd); DA2(dv.dlt, nd); DA2(dv.v, nd); DA2(dv.F, nd);
+    DA2(dv.sigma, Np); DA2(sys->inv_mass_store, Np); DA2(sys->st_f, nd);
+    DA2(dv.img, nd); DA2(dv.id, Np);
+    DA2(dv.gs0, Np * RF); DA2(dv.gs[0], Np * RF); DA2(dv.gs[1], Np * RF);
+    DA2(dv.gd[0], Np * RD); DA2(dv.gd[1], Np * RD);
+    DA2(dv.cell_count, dv.ncells); DA2(dv.cell_fill, dv.ncells); DA2(dv.cell_start, dv.ncells + 1);
+    DA2(dv.cell_of, Np); DA2(dv.perm, Np); DA2(dv.cellid, Np);
+    DA2(dv.tx, nd); DA2(dv.tv, nd); DA2(dv.tsig, Np); DA2(dv.tim, Np);
+    DA2(dv.timg, nd); DA2(dv.tid, Np);
+    DA2(dv.nnbr, Np);
+    dv.maxblocks = (int)((Np * 32 + 255) / 256);
+    DA2(dv.partials, (size_t)kNRed * dv.maxblocks);
+    DA2(dv.red, kNRed);
+    DA2(dv.flags, 1);
+    DA2(sys->st_x, nd); DA2(sys->st_v, nd); DA2(sys->st_m, Np); DA2(sys->st_sig, Np);
+    DA2(sys->st_i, nd); DA2(sys->st_cnt, Np); DA2(sys->st_off, Np + 1);
+    DA2(sys->snap_x0, nd); DA2(sys->snap_dlt, nd); DA2(sys->snap_v, nd); DA2(sys->snap_sig, Np);
+    DA2(sys->snap_im, Np); DA2(sys->snap_img, nd); DA2(sys->snap_id, Np);
+#undef DA2
+    if (cudaMallocHost((void **)&sys->h_flags, sizeof(Flags)) != cudaSuccess ||
+        cudaMallocHost((void **)&sys->h_red, sizeof(double) * kNRed) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(sys, HDMD_E_NOMEM, "pinned host allocation failed"));
+    }
+    if (cudaStreamCreateWithFlags(&sys->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sys->cap_stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sys->cap_stream3, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(sys, HDMD_E_CUDA, "stream creation failed"));
+    }
+    if (cudaMemsetAsync(dv.flags, 0, sizeof(Flags), sys->stream) != cudaSuccess ||
+        cudaMemsetAsync(dv.cell_count, 0, sizeof(int32_t) * dv.ncells, sys->stream) != cudaSuccess ||
+        cudaMemsetAsync(dv.nnbr, 0, sizeof(int32_t) * Np, sys->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(sys, HDMD_E_CUDA, "initial memset failed"));
+    }
+    dv.inv_mass = nullptr;   // unit masses until set_state says otherwise
+    st = alloc_lists(sys, initial_capacity(sys));
+    if (st) return bail(st);
+    // diameters in caller order (identity internal order until set_state)
+    if (cudaMemcpyAsync(sys->st_sig, diameters, sizeof(double) * N, cudaMemcpyHostToDevice,
+                        sys->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dv.sigma, sys->st_sig, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                        sys->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(sys, HDMD_E_CUDA, "diameter upload failed"));
+    }
+    if (cudaStreamSynchronize(sys->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(sys, HDMD_E_CUDA, "stream synchronize failed"));
+    }
+    *out = sys;
+    return HDMD_OK;
+}
+
+hdmd_status set_state(hdmd_system *sys, const double *x, const double *v, const double *masses) {
+    if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
+    if (!x) return fail(sys, HDMD_E_INVALID, "x is NULL");
+    const int64_t N = sys->N;
+    const int d = sys->d;
+    for (int64_t a = 0; a < N * d; ++a)
+        if (!std::isfinite(x[a]) || (v && !std::isfinite(v[a])))
+            return fail(sys, HDMD_E_INVALID, "non-finite position or velocity");
+    if (masses)
+        for (int64_t i = 0; i < N; ++i)
+            if (!(masses[i] > 0.0) || !std::isfinite(masses[i]))
+                return fail(sys, HDMD_E_INVALID, "masses must be positive and finite");
+    Dev &dv = sys->dv;
+    // diameters back to caller order before the internal order is reset
+    if (sys->have_state) {
+        launch_export(dv, nullptr, nullptr, nullptr, nullptr, sys->st_sig, sys->stream);
+        CKL(sys);
+    } else {
+        CK(cudaMemcpyAsync(sys->st_sig, dv.sigma, sizeof(double) * N, cudaMemcpyDeviceToDevice, sys->stream));
+    }
+    CK(cudaMemcpyAsync(sys->st_x, x, sizeof(double) * N * d, cudaMemcpyHostToDevice, sys->stream));
+    if (v) CK(cudaMemcpyAsync(sys->st_v, v, sizeof(double) * N * d, cudaMemcpyHostToDevice, sys->stream));
+    bool unit = true;
+    if (masses)
+        for (int64_t i = 0; i < N; ++i)
+            if (masses[i] != 1.0) { unit = false; break; }
+    sys->unit_mass = unit;
+    if (!unit)
+        CK(cudaMemcpyAsync(sys->st_m, masses, sizeof(double) * N, cudaMemcpyHostToDevice, sys->stream));
+    dv.inv_mass = unit ? nullptr : sys->inv_mass_store;   // NULL: all masses 1
+    const Dev d2 = dv;
+    launch_import(d2, sys->st_x, v ? sys->st_v : nullptr, unit ? nullptr : sys->st_m, sys->stream);
+    CKL(sys);
+    launch_import_sigma(dv, sys->st_sig, sys->stream);
+    CKL(sys);
+    sys->have_state = true;
+    free_graphs(sys);   // inv_mass pointer may have changed
+    return build_forced(sys, 0);
+}
+
+hdmd_status set_diameters(hdmd_system *sys, const double *diameters) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!diameters) return fail(sys, HDMD_E_INVALID, "diameters is NULL");
+    double smax = 0.0;
+    for (int64_t i = 0; i < sys->N; ++i) {
+        if (!(diameters[i] > 0.0) || !std::isfinite(diameters[i]))
+            return fail(sys, HDMD_E_INVALID, "diameters must be positive and finite");
+        smax = std::max(smax, diameters[i]);
+    }
+    if (smax > sys->sigma_max)
+        return fail(sys, HDMD_E_INVALID, "the largest diameter may not grow beyond its value at creation");
+    CK(cudaMemcpyAsync(sys->st_sig, diameters, sizeof(double) * sys->N, cudaMemcpyHostToDevice, sys->stream));
+    launch_import_sigma(sys->dv, sys->st_sig, sys->stream);
+    CKL(sys);
+    return build_forced(sys, sys->buf);
+}
+
+hdmd_status get_state(hdmd_system *sys, double *x, double *v, int32_t *img, double *f,
+                      double *diameters) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (f && !sys->F_valid) {
+        const bool fp64 = sys->prec == HDMD_FP64;
+        st = ensure_rows(sys, sys->buf, !fp64, fp64);
+        if (st) return st;
+        st = force_only(sys, sys->buf, fp64, false);
+        if (st) return st;
+        sys->F_valid = true;
+    }
+    const int64_t nd = sys->N * sys->d;
+    launch_export(sys->dv, x ? sys->st_x : nullptr, img ? sys->st_i : nullptr, v ? sys->st_v : nullptr,
+                  f ? sys->st_f : nullptr, diameters ? sys->st_sig : nullptr, sys->stream);
+    CKL(sys);
+    if (x) CK(cudaMemcpyAsync(x, sys->st_x, sizeof(double) * nd, cudaMemcpyDeviceToHost, sys->stream));
+    if (v) CK(cudaMemcpyAsync(v, sys->st_v, sizeof(double) * nd, cudaMemcpyDeviceToHost, sys->stream));
+    if (img) CK(cudaMemcpyAsync(img, sys->st_i, sizeof(int32_t) * nd, cudaMemcpyDeviceToHost, sys->stream));
+    if (f) CK(cudaMemcpyAsync(f, sys->st_f, sizeof(double) * nd, cudaMemcpyDeviceToHost, sys->stream));
+    if (diameters)
+        CK(cudaMemcpyAsync(diameters, sys->st_sig, sizeof(double) * sys->N, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    return HDMD_OK;
+}
+
+hdmd_status build_neighbors(hdmd_system *sys, int force, int *rebuilt) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    CK(cudaMemcpyAsync(&sys->h_flags->nbuilds, &sys->dv.flags->nbuilds, sizeof(int),
+                       cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    const int nb0 = sys->h_flags->nbuilds;
+    if (force) {
+        st = build_forced(sys, sys->buf);
+        if (st) return st;
+    } else {
+        st = clear_errors(sys);
+        if (st) return st;
+        launch_check_trigger(sys->dv, sys->stream);
+        launch_rebuild(sys->dv, sys->buf, true, sys->stream);
+        CKL(sys);
+        st = read_flags(sys);
+        if (st) return st;
+        if (sys->h_flags->nbuilds != nb0) {
+            sys->F_valid = false;
+            sys->rows32_valid = sys->rows64_valid = true;
+            if (sys->h_flags->error & ERR_OVERFLOW) {
+                st = grow_lists(sys);
+                if (st) return st;
+                st = build_forced(sys, sys->buf);
+                if (st) return st;
+            }
+        }
+        st = clear_flag_field(sys, offsetof(Flags, rebuild), sizeof(int));
+        if (st) return st;
+    }
+    CK(cudaMemcpyAsync(&sys->h_flags->nbuilds, &sys->dv.flags->nbuilds, sizeof(int),
+                       cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    if (rebuilt) *rebuilt = sys->h_flags->nbuilds != nb0;
+    return HDMD_OK;
+}
+
+hdmd_status get_neighbors(hdmd_system *sys, int32_t *counts, int32_t *idx, int64_t *total) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!counts) return fail(sys, HDMD_E_INVALID, "counts is NULL");
+    const int64_t N = sys->N;
+    launch_list_export(sys->dv, sys->st_cnt, nullptr, nullptr, sys->stream);
+    CKL(sys);
+    CK(cudaMemcpyAsync(counts, sys->st_cnt, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    std::vector<int64_t> off(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) off[i + 1] = off[i] + counts[i];
+    if (total) *total = off[N];
+    if (!idx || off[N] == 0) return HDMD_OK;
+    if (off[N] > sys->st_idx_cap) {
+        if (sys->st_idx) cudaFree(sys->st_idx);
+        sys->st_idx = nullptr;
+        if (cudaMalloc((void **)&sys->st_idx, sizeof(int32_t) * off[N]) != cudaSuccess) {
+            cudaGetLastError();
+            sys->st_idx_cap = 0;
+            return fail(sys, HDMD_E_NOMEM, "staging for get_neighbors failed");
+        }
+        sys->st_idx_cap = off[N];
+    }
+    CK(cudaMemcpyAsync(sys->st_off, off.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, sys->stream));
+    launch_list_export(sys->dv, nullptr, sys->st_idx, sys->st_off, sys->stream);
+    CKL(sys);
+    CK(cudaMemcpyAsync(idx, sys->st_idx, sizeof(int32_t) * off[N], cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    for (int64_t i = 0; i < N; ++i) std::sort(idx + off[i], idx + off[i + 1]);
+    return HDMD_OK;
+}
+
+hdmd_status compute_forces(hdmd_system *sys, double *energy, double *virial) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    const bool fp64 = sys->prec == HDMD_FP64;
+    st = ensure_rows(sys, sys->buf, !fp64, fp64);
+    if (st) return st;
+    st = force_only(sys, sys->buf, fp64, true);
+    if (st) return st;
+    sys->F_valid = true;
+    st = read_flags(sys);
+    if (st) return st;
+    if (energy) *energy = 0.5 * sys->h_red[R_E];
+    if (virial) *virial = 0.5 * sys->h_red[R_W];
+    return check_device_errors(sys);
+}
+
+hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (nsteps < 0) return fail(sys, HDMD_E_INVALID, "nsteps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(sys, HDMD_E_INVALID, "dt must be positive");
+    st = snapshot(sys, false);
+    if (st) return st;
+    const int buf0 = sys->buf;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        st = md_once(sys, nsteps, dt, last);
+        if (st != HDMD_E_NBR_OVERFLOW) return st;
+        // a build overflowed: restore the starting state, grow, and run again
+        st = snapshot(sys, true);
+        if (st) return st;
+        st = grow_lists(sys);
+        if (st) return st;
+        st = build_forced(sys, buf0);
+        if (st) return st;
+    }
+    return fail(sys, HDMD_E_NBR_OVERFLOW, "Verlet list kept overflowing during md_steps");
+}
+
+hdmd_status fire_minimize(hdmd_system *sys, const hdmd_fire_params *params, hdmd_fire_result *res) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    hdmd_fire_params p;
+    if (params) {
+        p = *params;
+    } else {
+        p.dt0 = 0.005; p.dt_max = 0.05; p.dt_min = 1e-4; p.f_inc = 1.1; p.f_dec = 0.5;
+        p.alpha0 = 0.25; p.f_alpha = 0.99; p.f_tol = 1e-10; p.polish_tol = 1e-6;
+        p.n_delay = 20; p.n_neg_max = 2000; p.max_iter = 1000000; p.initial_delay = 1;
+    }
+    if (!(p.dt0 > 0) || !(p.dt_max >= p.dt0) || !(p.dt_min > 0) || !(p.dt_min <= p.dt0) ||
+        !(p.f_inc >= 1) || !(p.f_dec > 0 && p.f_dec <= 1) || !(p.alpha0 >= 0 && p.alpha0 <= 1) ||
+        !(p.f_alpha > 0 && p.f_alpha <= 1) || !(p.f_tol >= 0) || p.max_iter < 0 || p.n_delay < 0 ||
+        p.n_neg_max < 0)
+        return fail(sys, HDMD_E_INVALID, "invalid FIRE parameters");
+    st = snapshot(sys, false);
+    if (st) return st;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        st = fire_once(sys, p, res);
+        if (st != HDMD_E_NBR_OVERFLOW) return st;
+        st = snapshot(sys, true);
+        if (st) return st;
+        st = grow_lists(sys);
+        if (st) return st;
+        st = build_forced(sys, 0);
+        if (st) return st;
+    }
+    return fail(sys, HDMD_E_NBR_OVERFLOW, "Verlet list kept overflowing during FIRE");
+}
+
+hdmd_status swap_sweep(hdmd_system *sys, int nsweeps, double T, double p, uint64_t seed,
+                       const int32_t *pairs, const double *uniforms, int64_t npairs,
+                       int64_t *accepted, uint8_t *accepted_flags) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!(T > 0.0) || std::isnan(T)) return fail(sys, HDMD_E_INVALID, "T must be positive");
+    const int64_t N = sys->N;
+    int M;
+    if (pairs) {
+        if (!uniforms) return fail(sys, HDMD_E_INVALID, "explicit pairs need uniforms");
+        if (npairs < 1 || npairs > (int64_t)1 << 26) return fail(sys, HDMD_E_INVALID, "npairs out of range");
+        for (int64_t k = 0; k < npairs; ++k) {
+            const int32_t i = pairs[2 * k], j = pairs[2 * k + 1];
+            if (i < 0 || j < 0 || i >= N || j >= N || i == j)
+                return fail(sys, HDMD_E_INVALID, "pair atoms must be distinct caller indices in [0, N)");
+            if (!(uniforms[k] >= 0.0 && uniforms[k] < 1.0))
+                return fail(sys, HDMD_E_INVALID, "uniforms must lie in [0, 1)");
+        }
+        M = (int)npairs;
+        nsweeps = 1;
+    } else {
+        if (nsweeps < 0) return fail(sys, HDMD_E_INVALID, "nsweeps must be >= 0");
+        if (!(p > 0.0 && p <= 1.0)) return fail(sys, HDMD_E_INVALID, "p must be in (0, 1]");
+        M = (int)std::max<int64_t>(1, std::llround(p * (double)N));
+    }
+    if (nsweeps == 0) { if (accepted) *accepted = 0; return HDMD_OK; }
+    st = swap_alloc(sys, M, std::max(sys->sw.scap, swap_list_estimate(sys)));
+    if (st) return st;
+    SwapDev &sw = sys->sw;
+    sw.npairs = M;
+    sw.T = T;
+    sw.rcut = sys->sigma_max;
+    st = ensure_rows(sys, sys->buf, true, sys->rows64_valid);
+    if (st) return st;
+    CK(cudaMemsetAsync(sw.nacc, 0, sizeof(unsigned long long), sys->stream));
+    for (int s = 0; s < nsweeps; ++s) {
+        if (pairs) {
+            CK(cudaMemcpyAsync(sw.ids, pairs, sizeof(int32_t) * 2 * M, cudaMemcpyHostToDevice, sys->stream));
+            CK(cudaMemcpyAsync(sw.u, uniforms, sizeof(double) * M, cudaMemcpyHostToDevice, sys->stream));
+        } else {
+            launch_swap_draw(sw, seed, s, (int)N, sys->stream);
+            CKL(sys);
+        }
+        st = swap_pass(sys);
+        if (st) return st;
+    }
+    unsigned long long nacc = 0;
+    CK(cudaMemcpyAsync(&sys->h_flags->total_entries, sw.nacc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    nacc = (unsigned long long)sys->h_flags->total_entries;
+    if (accepted) *accepted = (int64_t)nacc;
+    if (accepted_flags) {
+        std::vector<int8_t> stv(M);
+        CK(cudaMemcpyAsync(stv.data(), sw.state, M, cudaMemcpyDeviceToHost, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+        for (int k = 0; k < M; ++k) accepted_flags[k] = stv[k] == 2;
+    }
+    // diameters changed: the list radii and the rows' sigma/2 are stale
+    return build_forced(sys, sys->buf);
+}
+
+hdmd_status get_info(hdmd_system *sys, hdmd_info *info) {
+    if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
+    if (!info) return fail(sys, HDMD_E_INVALID, "info is NULL");
+    CK(cudaMemcpyAsync(sys->h_flags, sys->dv.flags, sizeof(Flags), cudaMemcpyDeviceToHost, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    info->d = sys->d;
+    info->N = sys->N;
+    info->L = sys->L;
+    info->n_cell = sys->dv.n;
+    info->n_cells = sys->dv.ncells;
+    info->list_capacity = sys->dv.cap;
+    info->lanes_per_atom = sys->dv.G;
+    info->max_list_length = sys->h_flags->max_count;
+    info->total_list_entries = sys->h_flags->total_entries;
+    info->precision = sys->prec;
+    info->graphs = sys->use_graphs && sys->graphs_ok;
+    info->device_bytes = sys->bytes;
+    return HDMD_OK;
+}
+
+hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs) {
+    if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
+    if (lanes_per_atom) {
+        if (lanes_per_atom < 1 || lanes_per_atom > 32 || (lanes_per_atom & (lanes_per_atom - 1)))
+            return fail(sys, HDMD_E_INVALID, "lanes_per_atom must be a power of two in 1..32");
+        sys->dv.G = lanes_per_atom;
+        hdmd_status st = alloc_lists(sys, sys->dv.cap);
+        if (st) return st;
+    }
+    if (use_graphs >= 0) {
+        sys->use_graphs = use_graphs ? 1 : 0;
+        if (use_graphs) sys->graphs_ok = true;
+    }
+    free_graphs(sys);
+    if (sys->have_state) return build_forced(sys, sys->buf);
+    return HDMD_OK;
+}
+
+hdmd_status destroy_system(hdmd_system *sys) {
+    if (!sys) return HDMD_OK;
+    if (sys->stream) cudaStreamSynchronize(sys->stream);
+    free_graphs(sys);
+    swap_free(sys);
+    for (void *p : sys->allocs) cudaFree(p);
+    if (sys->nbr) cudaFree(sys->nbr);
+    if (sys->code) cudaFree(sys->code);
+    if (sys->st_idx) cudaFree(sys->st_idx);
+    if (sys->h_flags) cudaFreeHost(sys->h_flags);
+    if (sys->h_red) cudaFreeHost(sys->h_red);
+    if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);
+    if (sys->cap_stream2) cudaStreamDestroy(sys->cap_stream2);
+    if (sys->cap_stream3) cudaStreamDestroy(sys->cap_stream3);
+    cudaGetLastError();
+    delete sys;
+    return HDMD_OK;
+}
+
+const char *hdmd_last_error(const hdmd_system *sys) {
+    if (sys) return sys->err.c_str();
+    return g_thread_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+"""Python binding of the hdmd C ABI (include/hdmd.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of ``libhdmd.so``; this module
+converts numpy arrays to the ABI's row-major host buffers and back.  There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.  Functions keep the ABI's names; ``System`` bundles them around one
+handle.  The CUDA stream defaults to PyTorch's current stream when PyTorch
+is importable with a GPU, else the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhdmd.so")
+
+HDMD_FP64, HDMD_MIXED = 0, 1
+STATUS = {0: "HDMD_OK", 1: "HDMD_E_INVALID", 2: "HDMD_E_NOMEM", 3: "HDMD_E_NBR_OVERFLOW",
+          4: "HDMD_E_LOST_ATOM", 5: "HDMD_E_NOT_CONVERGED", 6: "HDMD_E_CUDA",
+          7: "HDMD_E_TIMEOUT", 8: "HDMD_E_UNSUPPORTED_D"}
+
+
+class HDMDError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class Potential(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("skin", C.c_double)]
+
+
+class Thermo(C.Structure):
+    _fields_ = [("E_pair", C.c_double), ("virial", C.c_double), ("K", C.c_double),
+                ("T", C.c_double), ("P", C.c_double), ("steps", C.c_int64),
+                ("rebuilds", C.c_int64)]
+
+
+class FireParams(C.Structure):
+    _fields_ = [("dt0", C.c_double), ("dt_max", C.c_double), ("dt_min", C.c_double),
+                ("f_inc", C.c_double), ("f_dec", C.c_double), ("alpha0", C.c_double),
+                ("f_alpha", C.c_double), ("f_tol", C.c_double), ("polish_tol", C.c_double),
+                ("n_delay", C.c_int64), ("n_neg_max", C.c_int64), ("max_iter", C.c_int64),
+                ("initial_delay", C.c_int)]
+
+
+class FireResult(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("polish_iterations", C.c_int64),
+                ("rebuilds", C.c_int64), ("E_pair", C.c_double), ("fmax", C.c_double),
+                ("converged", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int64), ("L", C.c_double), ("n_cell", C.c_int),
+                ("n_cells", C.c_int64), ("list_capacity", C.c_int), ("lanes_per_atom", C.c_int),
+                ("max_list_length", C.c_int), ("total_list_entries", C.c_int64),
+                ("precision", C.c_int), ("graphs", C.c_int), ("device_bytes", C.c_int64)]
+
+
+FIRE_DEFAULTS = dict(dt0=0.005, dt_max=0.05, dt_min=1e-4, f_inc=1.1, f_dec=0.5, alpha0=0.25,
+                     f_alpha=0.99, f_tol=1e-10, polish_tol=1e-6, n_delay=20, n_neg_max=2000,
+                     max_iter=1000000, initial_delay=1)
+
+_lib = None
+
+
+def lib():
+    """Load libhdmd.so; raise if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("hdmd CUDA library not built (%s missing); run "
+                               "paper_2112_12271_gb300.build.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "create_system": [i32, i64, dbl, vp, vp, i32, vp, C.POINTER(vp)],
+            "set_state": [vp, vp, vp, vp],
+            "set_diameters": [vp, vp],
+            "get_state": [vp, vp, vp, vp, vp, vp],
+            "build_neighbors": [vp, i32, C.POINTER(i32)],
+            "get_neighbors": [vp, vp, vp, C.POINTER(i64)],
+            "compute_forces": [vp, C.POINTER(dbl), C.POINTER(dbl)],
+            "md_steps": [vp, i64, dbl, vp],
+            "fire_minimize": [vp, vp, vp],
+            "swap_sweep": [vp, i32, dbl, dbl, C.c_uint64, vp, vp, i64, C.POINTER(i64), vp],
+            "get_info": [vp, vp],
+            "set_tuning": [vp, i32, i32],
+            "destroy_system": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.hdmd_last_error.argtypes = [vp]
+        L.hdmd_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st, h=None):
+    if st != 0:
+        msg = lib().hdmd_last_error(h).decode(errors="replace")
+        raise HDMDError(st, msg)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ ABI calls
+def create_system(d, N, L, diameters, eps=1.0, skin=0.3, precision=HDMD_MIXED, stream=None):
+    diam = _f64(diameters)
+    if diam.shape != (N,):
+        raise ValueError("diameters must have shape (N,)")
+    pot = Potential(0, eps, skin)
+    h = C.c_void_p()
+    st = lib().create_system(d, N, L, _p(diam), C.byref(pot), int(precision),
+                             stream if stream is not None else default_stream(), C.byref(h))
+    _check(st)
+    return h
+
+
+def set_state(h, x, v=None, masses=None):
+    x = _f64(x)
+    v = None if v is None else _f64(v)
+    m = None if masses is None else _f64(masses)
+    _check(lib().set_state(h, _p(x), _p(v), _p(m)), h)
+
+
+def set_diameters(h, diameters):
+    _check(lib().set_diameters(h, _p(_f64(diameters))), h)
+
+
+def get_state(h, N, d, x=True, v=True, img=True, f=False, sigma=False):
+    out = {}
+    xa = np.empty((N, d)) if x else None
+    va = np.empty((N, d)) if v else None
+    ia = np.empty((N, d), dtype=np.int32) if img else None
+    fa = np.empty((N, d)) if f else None
+    sa = np.empty(N) if sigma else None
+    _check(lib().get_state(h, _p(xa), _p(va), _p(ia), _p(fa), _p(sa)), h)
+    for k, a in (("x", xa), ("v", va), ("img", ia), ("f", fa), ("sigma", sa)):
+        if a is not None:
+            out[k] = a
+    return out
+
+
+def build_neighbors(h, force=True):
+    r = C.c_int(0)
+    _check(lib().build_neighbors(h, 1 if force else 0, C.byref(r)), h)
+    return bool(r.value)
+
+
+def get_neighbors(h, N):
+    counts = np.empty(N, dtype=np.int32)
+    tot = C.c_int64(0)
+    _check(lib().get_neighbors(h, _p(counts), None, C.byref(tot)), h)
+    idx = np.empty(max(tot.value, 1), dtype=np.int32)
+    _check(lib().get_neighbors(h, _p(counts), _p(idx), C.byref(tot)), h)
+    return counts, idx[:tot.value]
+
+
+def compute_forces(h):
+    e, w = C.c_double(), C.c_double()
+    _check(lib().compute_forces(h, C.byref(e), C.byref(w)), h)
+    return e.value, w.value
+
+
+def md_steps(h, nsteps, dt):
+    t = Thermo()
+    _check(lib().md_steps(h, int(nsteps), float(dt), C.byref(t)), h)
+    return {k: getattr(t, k) for k, _ in Thermo._fields_}
+
+
+def fire_minimize(h, raise_on_fail=False, **params):
+    p = dict(FIRE_DEFAULTS)
+    p.update(params)
+    fp = FireParams(**p)
+    r = FireResult()
+    st = lib().fire_minimize(h, C.byref(fp), C.byref(r))
+    if st not in (0, 5) or (st == 5 and raise_on_fail):
+        _check(st, h)
+    out = {k: getattr(r, k) for k, _ in FireResult._fields_}
+    out["status"] = st
+    return out
+
+
+def swap_sweep(h, T, p=0.1, nsweeps=1, seed=0, pairs=None, uniforms=None):
+    acc = C.c_int64(0)
+    if pairs is not None:
+        pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        u = _f64(uniforms)
+        flags = np.zeros(len(pr), dtype=np.uint8)
+        _check(lib().swap_sweep(h, 1, float(T), float(p), C.c_uint64(seed), _p(pr), _p(u),
+                                len(pr), C.byref(acc), _p(flags)), h)
+        return acc.value, flags.astype(bool)
+    _check(lib().swap_sweep(h, int(nsweeps), float(T), float(p), C.c_uint64(seed), None, None,
+                            0, C.byref(acc), None), h)
+    return acc.value, None
+
+
+def get_info(h):
+    i = Info()
+    _check(lib().get_info(h, C.byref(i)), h)
+    return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+def set_tuning(h, lanes_per_atom=0, use_graphs=-1):
+    _check(lib().set_tuning(h, int(lanes_per_atom), int(use_graphs)), h)
+
+
+def destroy_system(h):
+    if h:
+        _check(lib().destroy_system(h))
+
+
+class System:
+    """One resident system: the ABI calls bound to a handle."""
+
+    def __init__(self, d, L, diameters, x=None, v=None, masses=None, eps=1.0, skin=0.3,
+                 precision=HDMD_MIXED, stream=None):
+        self.d, self.L = int(d), float(L)
+        self.N = int(np.asarray(diameters).shape[0])
+        self.h = create_system(self.d, self.N, self.L, diameters, eps, skin, precision, stream)
+        if x is not None:
+            self.set_state(x, v, masses)
+
+    def set_state(self, x, v=None, masses=None):
+        set_state(self.h, x, v, masses)
+
+    def set_diameters(self, diameters):
+        set_diameters(self.h, diameters)
+
+    def state(self, **kw):
+        return get_state(self.h, self.N, self.d, **kw)
+
+    def build_neighbors(self, force=True):
+        return build_neighbors(self.h, force)
+
+    def neighbors(self):
+        return get_neighbors(self.h, self.N)
+
+    def forces(self):
+        e, w = compute_forces(self.h)
+        f = get_state(self.h, self.N, self.d, x=False, v=False, img=False, f=True)["f"]
+        return f, e, w
+
+    def md_steps(self, nsteps, dt):
+        return md_steps(self.h, nsteps, dt)
+
+    def fire(self, **params):
+        return fire_minimize(self.h, **params)
+
+    def swap(self, T, **kw):
+        return swap_sweep(self.h, T, **kw)
+
+    def info(self):
+        return get_info(self.h)
+
+    def tune(self, lanes_per_atom=0, use_graphs=-1):
+        set_tuning(self.h, lanes_per_atom, use_graphs)
+
+    def close(self):
+        if self.h:
+            destroy_system(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,67 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+function include/hdmd.h declares (no compute calls: there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hdmd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_][a-z_0-9]*\s*\**\s*([a-z_][a-z_0-9]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2112_12271_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("create_system", "set_state", "get_state", "build_neighbors", "get_neighbors",
+              "compute_forces", "md_steps", "fire_minimize", "swap_sweep", "destroy_system",
+              "hdmd_last_error"):
+        assert n in names, n
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_errors_without_gpu_are_reported_not_raised(libpath):
+    # argument validation happens before any device work
+    from paper_2112_12271_gb300 import hdmd
+    lib = hdmd.lib()
+    h = ctypes.c_void_p()
+    pot = hdmd.Potential(0, 1.0, 0.3)
+    import numpy as np
+    diam = np.ones(10)
+    st = lib.create_system(11, 10, 5.0, diam.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
+    assert st == 8   # HDMD_E_UNSUPPORTED_D
+    assert b"d must be" in lib.hdmd_last_error(None)
+    st = lib.create_system(3, 10, 2.0, diam.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
+    assert st == 1   # box too small for two subcells
+    assert b"box too small" in lib.hdmd_last_error(None)
+    bad = diam.copy(); bad[3] = -1.0
+    st = lib.create_system(3, 10, 9.0, bad.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
+    assert st == 1
+    assert lib.destroy_system(None) == 0
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2112_12271_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "hdmd_oracle" not in txt, f
