@@ -1,0 +1,322 @@
+"""Benchmark: MD throughput of the d=6, N=32768 polydisperse harmonic system.
+
+One bench step = 1000 velocity-Verlet timesteps (dt = 0.005, skin 0.3, with
+the on-device rebuild trigger and list builds) of a resident system through
+the C ABI (md_steps).  Metric: atom-steps/s = N x timesteps / device time.
+The system (box side 6, N = 32768, diameters U[0.8, 1.2], T = 1e-3) is
+synthetic, drawn with a fixed seed.  Its working set (~40 MB) fits in the
+129 MB L2, so L2 is flushed (a 512 MB buffer written) before each timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--gpus N > 1 runs under torchrun as N independent replicas (one per GPU; the
+method has no cross-replica exchange): weak scaling, value = all ranks'
+atom-steps / the slowest rank's time.  --impl reference times the FP64 CPU
+oracle on the host instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2112_12271_gb300 import workloads as W  # noqa: E402
+
+MD_PER_STEP = 1000
+DT = 0.005
+METRIC = "atom-steps/s at d=6 N=32768 (mixed FP32-pair/FP64 VV)"
+UNIT = "atom-steps/s"
+WORKLOAD = "d6_N32768_polydisperse_harmonic_L6_NVE_dt0.005_skin0.3"
+# c1: the benchmark system; c1l: the same density with N = 2^21 (L = 12), whose
+# working set exceeds L2 (the HBM-bound case used for ncu captures)
+WORKLOADS = {"c1": 32768, "c1l": 2 ** 21}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [t.strip() for t in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = float(p[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- CPU arms
+def oracle_md_sample(sysd, nsteps):
+    """Time the FP64 oracle on nsteps of the workload (list build included)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    out = oracle.md_steps(sysd.x, sysd.v, sysd.sigma, sysd.L, nsteps, DT)
+    dt = time.perf_counter() - t0
+    return dt, out
+
+
+def cpu_baseline(sysd, nsteps=100):
+    dt, _ = oracle_md_sample(sysd, nsteps)
+    return {"value": sysd.N * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d VV timesteps of the same d=6 N=32768 system (one cell-list "
+                      "build + %d force evaluations), serial FP64 C, %.1f s" % (nsteps, nsteps, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    s = W.c1_poly_d6()
+    per = 20    # oracle timesteps per bench step (a bounded sample)
+    for _ in range(args.warmup):
+        oracle_md_sample(s, 5)
+    t = 0.0
+    for _ in range(args.steps):
+        dt, _ = oracle_md_sample(s, per)
+        t += dt
+    value = s.N * per * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": s.N, "d": 6,
+                       "timesteps_per_step": per, "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d VV timesteps per step, serial FP64 C oracle "
+                                       "(list build each step)" % per},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2112_12271_gb300 import build as B
+    from paper_2112_12271_gb300 import hdmd
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+        B.build()
+
+    s = W.c1_poly_d6(seed=rank, N=WORKLOADS[args.workload])
+    md_per_step = args.md_per_step
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed_md(g, K, W_):
+        for _ in range(W_):
+            g.md_steps(md_per_step, DT)
+        ms, rebuilds = [], 0
+        for _ in range(K):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t = g.md_steps(md_per_step, DT)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            rebuilds += t["rebuilds"]
+        return ms, rebuilds, t
+
+    g = hdmd.System(s.d, s.L, s.sigma, s.x, s.v, precision=hdmd.HDMD_MIXED,
+                    stream=stream.cuda_stream)
+    if args.eager:
+        g.tune(use_graphs=0)   # profilers cannot see kernels inside conditional graphs
+    info = g.info()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev)
+    clk.start()
+    ms, rebuilds, last = timed_md(g, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total_ms = sum(ms)
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = ws * s.N * md_per_step * args.steps / (total_ms / 1000.0)
+    info = g.info()
+    prof = g.profile(reps=50, dt=DT) if not args.no_profile else None
+
+    # end to end: host state in (pinned), md_steps, thermo out, per step
+    xh = torch.from_numpy(np.ascontiguousarray(s.x)).pin_memory().numpy()
+    vh = torch.from_numpy(np.ascontiguousarray(s.v)).pin_memory().numpy()
+    e2e_ms = []
+    for k in range(0 if args.no_e2e else args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_state(xh, vh)
+        g.md_steps(md_per_step, DT)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_value = (ws * s.N * md_per_step * args.steps / (sum(e2e_ms) / 1000.0)) if e2e_ms else None
+    g.close()
+
+    # FP64 plain form of the same workload (fewer steps: FP64 is slow on GB300)
+    fp64 = None
+    if not args.no_fp64:
+        g64 = hdmd.System(s.d, s.L, s.sigma, s.x, s.v, precision=hdmd.HDMD_FP64,
+                          stream=stream.cuda_stream)
+        k64 = max(1, min(args.steps, 3))
+        ms64, _, _ = timed_md(g64, k64, 1)
+        prof64 = g64.profile(reps=20, dt=DT) if not args.no_profile else None
+        g64.close()
+        fp64 = {"value": s.N * md_per_step * k64 / (sum(ms64) / 1000.0), "unit": UNIT,
+                "ms_per_step": sum(ms64) / k64, "steps": k64, "kernel_ms": prof64}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel: fused force + kicks + drift (mixed)
+    d = s.d
+    RF = (d + 1 + 3) & ~3
+    Z = info["total_list_entries"] / s.N
+    bytes_per_atom = 8 * Z + 4 + 16 * d + 16 * d + 3 * 4 * RF
+    achieved = bytes_per_atom * s.N / (prof["step_ms"] * 1e-3) / 1e9 if prof else None
+    peak, peak_kind = peaks()
+    n_launch = args.steps * (md_per_step + 1) + 6 * rebuilds
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-pair/f64-accumulate",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "c1" else
+                   "d6_N%d_polydisperse_harmonic_L%.0f_NVE_dt0.005_skin0.3" % (s.N, s.L),
+                   "N": s.N, "d": d, "L": s.L,
+                   "timesteps_per_step": md_per_step, "dt": DT, "skin": 0.3,
+                   "l2": "flushed (512 MB write) before each timed step",
+                   "n_cell": info["n_cell"], "mean_list_length": Z,
+                   "lanes_per_atom": info["lanes_per_atom"], "graphs": info["graphs"],
+                   "rebuilds_per_step": rebuilds / args.steps},
+        "fp64": fp64,
+        "kernel_ms": prof,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "k_step<6,mixed> (pair forces + kicks + drift)",
+                     "bytes_per_atom": bytes_per_atom, "peak_kind": peak_kind},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * s.N * d * 8,
+                "d2h_bytes_per_step": 7 * 8},
+        "gpu_launches": n_launch,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(s)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--md-per-step", type=int, default=MD_PER_STEP)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch kernels one by one instead of CUDA graphs (for ncu)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -184,6 +184,16 @@ hdmd_status swap_sweep(hdmd_system *sys, int nsweeps, double T, double p,
 hdmd_status get_info(hdmd_system *sys, hdmd_info *info);
 hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs);
 
+/* Benchmark support, not part of the method: average device time in
+ * milliseconds of single kernels on the current state, each launch timed
+ * alone with a CUDA event pair on the system's stream and averaged over reps
+ * launches.  ms_out[0]: the fused MD kernel (pair forces over the list, both
+ * half kicks, drift, trigger reduction) with time step dt; ms_out[1]: one
+ * full list build (wrap, binning, counting sort, reorder, Verlet lists);
+ * ms_out[2]: the force-only kernel.  The state (positions, velocities,
+ * lists) is restored before returning. */
+hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_out);
+
 /* Free everything the system holds.  NULL is accepted. */
 hdmd_status destroy_system(hdmd_system *sys);
 

@@ -80,7 +80,7 @@ def _load():
             lib.orc_kinetic.argtypes = [i32, i64, vp, vp]
             lib.orc_md_steps.restype = i64
             lib.orc_md_steps.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl,
-                                         dbl, i64, vp, vp]
+                                         dbl, i64, vp, i32, vp]
             lib.orc_fire.restype = i32
             lib.orc_fire.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl, vp,
                                      vp, vp]
@@ -200,13 +200,11 @@ def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None,
     sigma = _f64(sigma)
     m = None if mass is None else _f64(mass)
     img = np.zeros((N, d), dtype=np.int32) if img is None else np.array(img, dtype=np.int32)
-    if F is None:
-        F, _, _ = forces(x, sigma, L, eps, neighbors_brute(x, sigma, L, skin)
-                         if N <= 4096 else None)
-    F = _f64(F).copy()
+    have_F = F is not None
+    F = np.zeros_like(x) if F is None else _f64(F).copy()
     th = np.zeros(3)
     b = _load().orc_md_steps(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
-                             dt, int(nsteps), _p(F), _p(th))
+                             dt, int(nsteps), _p(F), int(have_F), _p(th))
     return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b))
 
 

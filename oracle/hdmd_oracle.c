@@ -344,13 +344,14 @@ static void vl_build(orc_vl *vl, int d, int64_t N, double L, const double *x,
                   int32_t *, int32_t *, int64_t) =
         n > 3 ? orc_neighbors_cells : orc_neighbors_brute;
     if (!vl->counts) vl->counts = malloc(sizeof(int32_t) * (size_t)N);
-    /* first pass counts, second pass fills */
-    int64_t tot = fn(d, N, L, x, sigma, skin, 0, vl->counts, NULL, 0);
-    if (tot + 1 > vl->cap) {
-        vl->cap = tot + tot / 2 + 16;
+    if (!vl->idx) {
+        vl->cap = 64 * N + 16;
+        vl->idx = malloc(sizeof(int32_t) * (size_t)vl->cap);
+    }
+    while (fn(d, N, L, x, sigma, skin, 0, vl->counts, vl->idx, vl->cap) < 0) {
+        vl->cap *= 2;
         vl->idx = realloc(vl->idx, sizeof(int32_t) * (size_t)vl->cap);
     }
-    fn(d, N, L, x, sigma, skin, 0, vl->counts, vl->idx, vl->cap);
     if (!vl->x0) vl->x0 = malloc(sizeof(double) * (size_t)(N * d));
     memcpy(vl->x0, x, sizeof(double) * (size_t)(N * d));
     vl->builds++;
@@ -397,17 +398,19 @@ static double wrap(double x, double L, int32_t *img)
  *   v += (dt/2) F/m;  x += dt v, wrapped with image counts;
  *   rebuild the Verlet list if the trigger fires;  F = F(x);
  *   v += (dt/2) F/m.
- * F must hold the forces at the incoming x and holds those at the outgoing
- * x on return.  thermo[0..2] = E_pair, virial W, kinetic K at the end.
+ * F must hold the forces at the incoming x (have_F != 0) or is computed
+ * first from the list (have_F == 0); it holds those at the outgoing x on
+ * return.  thermo[0..2] = E_pair, virial W, kinetic K at the end.
  * Returns the number of list builds (the first one included). */
 int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *img,
                      const double *sigma, const double *mass, double eps,
-                     double skin, double dt, int64_t nsteps, double *F,
+                     double skin, double dt, int64_t nsteps, double *F, int have_F,
                      double *thermo)
 {
     orc_vl vl = {0};
     double E = 0.0, W = 0.0;
     vl_build(&vl, d, N, L, x, sigma, skin);
+    if (!have_F) orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
     for (int64_t step = 0; step < nsteps; ++step) {
         for (int64_t i = 0; i < N; ++i) {
             double m = mass ? mass[i] : 1.0;

@@ -67,7 +67,9 @@ struct Flags {
     int error;               // ErrBits
     int max_count;           // longest list seen by the last build
     int nbuilds;             // builds since creation
-    int pad0;
+    int pad0;                // host scratch for small reads
+    unsigned int disp_bits;  // max |dlt|^2 of the running step (float bits)
+    int pad1;
     long long total_entries; // sum of list lengths at the last build
     double fire[FS_COUNT];
 };
@@ -86,6 +88,8 @@ struct Dev {
     // binning scratch (old order copies during a build)
     int32_t *cell_count, *cell_fill, *cell_start, *cell_of, *perm;
     int32_t *cellid;        // subcell of each internal slot at the last build
+    int32_t *batch_start;   // [ncells+1] exclusive scan of ceil(count / home_batch(d))
+    float hmax_f;           // largest radius (sigma_max / 2)
     double *tx, *tv, *tsig, *tim;
     int32_t *timg, *tid;
     // lists
@@ -96,6 +100,9 @@ struct Dev {
     int maxblocks;
     Flags *flags;
 };
+
+// home atoms held in registers by one warp of the list build
+__host__ __device__ constexpr int home_batch(int d) { return d <= 7 ? 8 : 4; }
 
 template <int D> struct Rows {
     static constexpr int RF = (D + 1 + 3) & ~3;   // floats per FP32 row

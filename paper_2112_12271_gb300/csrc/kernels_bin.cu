@@ -98,45 +98,54 @@ __global__ void k_assign(Dev dv, bool guarded) {
     atomicAdd(&dv.cell_count[cell], 1);
 }
 
-// step 2: exclusive scan of the histogram (one block); zero the counters
+// step 2: exclusive scans (one block) of the histogram -> cell_start, and of
+// the number of home batches per cell -> batch_start; zero the counters
 __global__ void __launch_bounds__(1024) k_scan(Dev dv, bool guarded) {
     if (skip(dv, guarded)) return;
-    __shared__ int warp_sums[32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ int warp_sums[2][32];
+    __shared__ int carry[2];
+    const int H = home_batch(dv.d);
+    if (threadIdx.x < 2) carry[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int base = 0; base < dv.ncells; base += 1024) {
-        int c = base + threadIdx.x;
-        int v = c < dv.ncells ? dv.cell_count[c] : 0;
-        int incl = v;
+        const int c = base + threadIdx.x;
+        const int v = c < dv.ncells ? dv.cell_count[c] : 0;
+        const int vb = (v + H - 1) / H;
+        int incl = v, inclb = vb;
         for (int o = 1; o < 32; o <<= 1) {
             int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+            int tb = __shfl_up_sync(0xffffffffu, inclb, o);
+            if (lane >= o) { incl += t; inclb += tb; }
         }
-        if (lane == 31) warp_sums[warp] = incl;
+        if (lane == 31) { warp_sums[0][warp] = incl; warp_sums[1][warp] = inclb; }
         __syncthreads();
-        if (warp == 0) {
-            int w = warp_sums[lane];
+        if (warp < 2) {
+            int w = warp_sums[warp][lane];
             int wi = w;
             for (int o = 1; o < 32; o <<= 1) {
                 int t = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += t;
             }
-            warp_sums[lane] = wi - w;   // exclusive warp offsets
+            warp_sums[warp][lane] = wi - w;   // exclusive warp offsets
         }
         __syncthreads();
-        int excl = carry + warp_sums[warp] + incl - v;
+        const int excl = carry[0] + warp_sums[0][warp] + incl - v;
+        const int exclb = carry[1] + warp_sums[1][warp] + inclb - vb;
         if (c < dv.ncells) {
             dv.cell_start[c] = excl;
+            dv.batch_start[c] = exclb;
             dv.cell_fill[c] = 0;
             dv.cell_count[c] = 0;
         }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
+        if (threadIdx.x == 1023) { carry[0] = excl + v; carry[1] = exclb + vb; }
         __syncthreads();
     }
-    if (threadIdx.x == 0) dv.cell_start[dv.ncells] = carry;
+    if (threadIdx.x == 0) {
+        dv.cell_start[dv.ncells] = carry[0];
+        dv.batch_start[dv.ncells] = carry[1];
+    }
 }
 
 // step 3: scatter into cell order (order inside a cell fixed by step 4)

@@ -20,45 +20,88 @@
 // A launch with kick2 + kick1_drift does "F_n; kick(F_n); kick(F_n); drift",
 // i.e. the end of step n-1 and the start of step n, reading the gather rows
 // of x_n and writing those of x_{n+1} into the other buffer.
+#include <type_traits>
+
 #include "launch.h"
 
 namespace hdmd {
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 128;   // one wave of blocks at the benchmark size
 
+// Displacement trigger, shared by the MD and FIRE update kernels: every
+// block folds its max |dlt|^2 (float bits: non-negative floats order as
+// unsigned integers, NaN above all) into flags->disp_bits; the last block
+// (ticket, no waiting) turns it into the rebuild flag and, inside a CUDA
+// graph, into the IF condition, then clears the word for the next launch.
+__device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bool blk_bad,
+                                             unsigned long long cond) {
+    __shared__ bool last;
+    unsigned bits = __float_as_uint(blk_max_d2);
+    bits = __reduce_max_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax(&dv.flags->disp_bits, bits);
+    if (blk_bad && (threadIdx.x & 31) == 0) atomicOr(&dv.flags->error, (int)ERR_LOST);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(&dv.flags->counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned b = atomicExch(&dv.flags->disp_bits, 0u);
+        const float d2 = __uint_as_float(b);
+        const float s2 = (float)(dv.skin * dv.skin) * (1.0f - 1e-5f);
+        const bool finite = d2 <= 3.0e38f;
+        const int trig = (4.0f * d2 > s2) || !finite;
+        if (!finite || 16.0 * (double)d2 > dv.L * dv.L) atomicOr(&dv.flags->error, (int)ERR_LOST);
+        dv.flags->rebuild = trig;
+        if (cond) cudaGraphSetConditional(cond, trig ? 1u : 0u);
+        dv.flags->counter = 0u;
+    }
+}
+
+// The MD / force kernel.  Phase A: G lanes per atom accumulate the pair
+// forces over the list and meet through xor shuffles; lane 0 parks the force
+// in shared memory.  Phase B: the block's (atom, axis) items are spread over
+// all threads, so the FP64 kick/drift arithmetic (the slow pipe on this GPU)
+// runs with every lane busy and every SoA access coalesced.  Phase C writes
+// the new gather rows (contiguous for the block) and folds the trigger.
 template <int D, bool FP64P>
 __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
+    using FT = typename std::conditional<FP64P, double, float>::type;
     constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
     __shared__ double sh[(NT / 32) * kNRed];
-    const int G = dv.G;
-    const int gt = blockIdx.x * NT + threadIdx.x;
-    const int i = gt / G;
-    const int g = gt - i * G;
-    const bool valid = i < dv.N;
+    __shared__ FT sF[NT * D];
+    __shared__ FT sE[NT], sW[NT];
+    __shared__ float sD2[NT];
+    __shared__ float sPos[FP64P ? 1 : NT * RF];
+    __shared__ int sBad;
     if (cfg.fire_red && dv.flags->fire[FS_STATUS] != (double)FIRE_RUNNING) return;  // loop ended
+    const int G = dv.G, APB = NT / G;
+    const int al = threadIdx.x / G, g = threadIdx.x - al * G;
+    const int base = blockIdx.x * APB;
+    const int i = base + al;
+    const bool valid = i < dv.N;
+    const int Np = dv.Npad;
+    if (threadIdx.x == 0) sBad = 0;
 
-    double acc[kNRed];
-#pragma unroll
-    for (int r = 0; r < kNRed; ++r) acc[r] = 0.0;
-
-    double Fi[D];
-    double e_i = 0.0, w_i = 0.0;
     if (cfg.compute_force) {
-        if (FP64P) {
-            double f[D];
+        FT f[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) f[k] = 0.0;
-            double e = 0.0, w = 0.0;
-            if (valid) {
+        for (int k = 0; k < D; ++k) f[k] = 0;
+        FT e = 0, w = 0;
+        if (valid) {
+            const int nn = dv.nnbr[i];
+            if (FP64P) {
                 const double *ri = dv.gd[cfg.in_buf] + (size_t)i * RD;
                 double xi[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) xi[k] = ri[k];
                 const double hi = ri[D];
-                const int nn = dv.nnbr[i];
                 for (int m = g; m < nn; m += G) {
-                    const int j = dv.nbr[list_pos(m, i, dv.Npad, G)];
+                    const int j = dv.nbr[list_pos(m, i, Np, G)];
                     const double *rj = dv.gd[cfg.in_buf] + (size_t)j * RD;
                     double dx[D], r2 = 0.0;
 #pragma unroll
@@ -74,28 +117,12 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
                         const double gg = 1.0 - r / s;
                         const double fr = r > 0.0 ? (dv.eps / s) * gg / r : 0.0;
 #pragma unroll
-                        for (int k = 0; k < D; ++k) f[k] += fr * dx[k];
-                        e += 0.5 * dv.eps * gg * gg;
-                        w += fr * r2;
+                        for (int k = 0; k < D; ++k) f[k] += (FT)(fr * dx[k]);
+                        e += (FT)(0.5 * dv.eps * gg * gg);
+                        w += (FT)(fr * r2);
                     }
                 }
-            }
-            for (int o = G >> 1; o > 0; o >>= 1) {
-#pragma unroll
-                for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
-                e += __shfl_xor_sync(0xffffffffu, e, o);
-                w += __shfl_xor_sync(0xffffffffu, w, o);
-            }
-#pragma unroll
-            for (int k = 0; k < D; ++k) Fi[k] = f[k];
-            e_i = e;
-            w_i = w;
-        } else {
-            float f[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) f[k] = 0.f;
-            float e = 0.f, w = 0.f;
-            if (valid) {
+            } else {
                 const float *ri = dv.gs[cfg.in_buf] + (size_t)i * RF;
                 float xi[D];
 #pragma unroll
@@ -103,182 +130,189 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
                 const float hi = ri[D];
                 const float Lsc = dv.Lsc_f;
                 const float eps = (float)dv.eps;
-                const int nn = dv.nnbr[i];
-                for (int m = g; m < nn; m += G) {
-                    const int64_t pos = list_pos(m, i, dv.Npad, G);
-                    const int j = dv.nbr[pos];
-                    const uint32_t code = dv.code[pos];
-                    const float4 *rj4 = reinterpret_cast<const float4 *>(dv.gs[cfg.in_buf] + (size_t)j * RF);
-                    float rj[RF];
+                constexpr int U = 4;   // list entries in flight per lane
+                for (int m0 = g; m0 < nn; m0 += U * G) {
+                    int jv[U];
+                    uint32_t cv[U];
 #pragma unroll
-                    for (int q = 0; q < RF / 4; ++q) {
-                        float4 t = __ldg(rj4 + q);
-                        rj[4 * q] = t.x; rj[4 * q + 1] = t.y; rj[4 * q + 2] = t.z; rj[4 * q + 3] = t.w;
+                    for (int u = 0; u < U; ++u) {
+                        const int m = m0 + u * G;
+                        const bool ok = m < nn;
+                        const int64_t pos = list_pos(ok ? m : g, i, Np, G);
+                        jv[u] = ok ? dv.nbr[pos] : -1;
+                        cv[u] = ok ? dv.code[pos] : 0u;
                     }
-                    float dx[D], r2 = 0.f;
+                    float rj[U][RF];
 #pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const float o = (float)((int)((code >> (2 * k)) & 3u) - 1);
-                        const float t = fmaf(-o, Lsc, xi[k] - rj[k]);
-                        dx[k] = t;
-                        r2 = fmaf(t, t, r2);
+                    for (int u = 0; u < U; ++u) {
+                        const float4 *rj4 = reinterpret_cast<const float4 *>(
+                            dv.gs[cfg.in_buf] + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF);
+#pragma unroll
+                        for (int q = 0; q < RF / 4; ++q) {
+                            const float4 t = __ldg(rj4 + q);
+                            rj[u][4 * q] = t.x; rj[u][4 * q + 1] = t.y;
+                            rj[u][4 * q + 2] = t.z; rj[u][4 * q + 3] = t.w;
+                        }
                     }
-                    const float s = hi + rj[D];
-                    if (r2 < s * s && r2 > 0.f) {
-                        const float inv_s = __frcp_rn(s);
-                        const float rinv = rsqrtf(r2);
-                        const float r = r2 * rinv;
-                        const float gg = fmaf(-r, inv_s, 1.f);
-                        const float fr = eps * inv_s * gg * rinv;
 #pragma unroll
-                        for (int k = 0; k < D; ++k) f[k] = fmaf(fr, dx[k], f[k]);
-                        e = fmaf(0.5f * eps * gg, gg, e);
-                        w = fmaf(fr, r2, w);
+                    for (int u = 0; u < U; ++u) {
+                        if (jv[u] < 0) continue;
+                        const uint32_t code = cv[u];
+                        float dx[D], r2 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            const float o = (float)((int)((code >> (2 * k)) & 3u) - 1);
+                            const float t = fmaf(-o, Lsc, xi[k] - rj[u][k]);
+                            dx[k] = t;
+                            r2 = fmaf(t, t, r2);
+                        }
+                        const float s = hi + rj[u][D];
+                        if (r2 < s * s && r2 > 0.f) {
+                            const float inv_s = __frcp_rn(s);
+                            const float rinv = rsqrtf(r2);
+                            const float r = r2 * rinv;
+                            const float gg = fmaf(-r, inv_s, 1.f);
+                            const float fr = eps * inv_s * gg * rinv;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+                            e = (FT)fmaf(0.5f * eps * gg, gg, (float)e);
+                            w = (FT)fmaf(fr, r2, (float)w);
+                        }
                     }
                 }
             }
-            for (int o = G >> 1; o > 0; o >>= 1) {
-#pragma unroll
-                for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
-                e += __shfl_xor_sync(0xffffffffu, e, o);
-                w += __shfl_xor_sync(0xffffffffu, w, o);
-            }
-#pragma unroll
-            for (int k = 0; k < D; ++k) Fi[k] = (double)f[k];
-            e_i = (double)e;
-            w_i = (double)w;
         }
-    } else {
+        for (int o = G >> 1; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) Fi[k] = valid ? dv.F[(size_t)k * dv.Npad + i] : 0.0;
+            for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) sF[al * D + k] = f[k];
+            sE[al] = e;
+            sW[al] = w;
+        }
     }
+    if (g == 0) sD2[al] = 0.f;
+    __syncthreads();
 
-    if (valid && g == 0) {
-        const int Np = dv.Npad;
-        if (cfg.store_F) {
+    // ---- phase B: (axis, atom) items
+    double acc[kNRed];
 #pragma unroll
-            for (int k = 0; k < D; ++k) dv.F[(size_t)k * Np + i] = Fi[k];
-        }
-        const double im = dv.inv_mass ? dv.inv_mass[i] : 1.0;
-        double v[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) v[k] = dv.v[(size_t)k * Np + i];
-        if (cfg.kick2) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) v[k] += cfg.halfdt * Fi[k] * im;
-        }
-        if (cfg.thermo) {
-            double v2 = 0.0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) v2 += v[k] * v[k];
-            acc[R_E] = e_i;
-            acc[R_W] = w_i;
-            acc[R_K2] = v2 / im;
-        }
+    for (int r = 0; r < kNRed; ++r) acc[r] = 0.0;
+    const bool merged = cfg.kick2 && cfg.kick1_drift;
+    const double kick = merged ? cfg.dt : cfg.halfdt;
+    const bool do_kick = cfg.kick2 || cfg.kick1_drift;
+    for (int t = threadIdx.x; t < APB * D; t += NT) {
+        const int k = t / APB, a = t - k * APB, ii = base + a;
+        if (ii >= dv.N) continue;
+        const size_t o = (size_t)k * Np + ii;
+        const double F = cfg.compute_force ? (double)sF[a * D + k] : dv.F[o];
+        if (cfg.store_F) dv.F[o] = F;
+        const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
+        const double Fm = dv.inv_mass ? F * im : F;
+        double v = dv.v[o];
+        if (do_kick) v += kick * Fm;
+        if (cfg.thermo) acc[R_K2] += v * v / im;
         if (cfg.fire_red) {
-            double P = 0.0, vv = 0.0, vf = 0.0, ff = 0.0, fn = 0.0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                P += Fi[k] * v[k];
-                vv += v[k] * v[k];
-                vf += v[k] * Fi[k] * im;
-                ff += (Fi[k] * im) * (Fi[k] * im);
-                fn += Fi[k] * Fi[k];
-            }
-            acc[R_E] = e_i;
-            acc[R_P] = P;
-            acc[R_VV] = vv;
-            acc[R_VF] = vf;
-            acc[R_FF] = ff;
-            acc[R_FN] = fn;
-            acc[R_FMAX2] = fn;
-            if (!(fn < INFINITY)) acc[R_BAD] = 1.0;
+            acc[R_P] += F * v;
+            acc[R_VV] += v * v;
+            acc[R_VF] += v * Fm;
+            acc[R_FF] += Fm * Fm;
+            acc[R_FN] += F * F;
         }
         if (cfg.kick1_drift) {
-            double d2 = 0.0;
-            bool bad = false;
-            float *go = dv.gs[cfg.out_buf] + (size_t)i * RF;
-            const float *g0 = dv.gs0 + (size_t)i * RF;
-            double *gdo = dv.gd[cfg.out_buf] + (size_t)i * RD;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                v[k] += cfg.halfdt * Fi[k] * im;
-                const size_t o = (size_t)k * Np + i;
-                const double dl = dv.dlt[o] + cfg.dt * v[k];
-                dv.dlt[o] = dl;
-                d2 += dl * dl;
-                if (FP64P) gdo[k] = dv.x0[o] + dl;
-                else go[k] = g0[k] + (float)dl;
-                bad |= !(fabs(dl) < INFINITY) || !(fabs(v[k]) < INFINITY);
-            }
-            if (FP64P) gdo[D] = 0.5 * dv.sigma[i];
-            else go[D] = g0[D];
-            acc[R_DMAX2] = d2;
-            if (bad) acc[R_BAD] = 1.0;
+            const double dl = dv.dlt[o] + cfg.dt * v;
+            dv.dlt[o] = dl;
+            const float fl = (float)dl;
+            atomicAdd(&sD2[a], fl * fl);
+            if (FP64P) dv.gd[cfg.out_buf][(size_t)ii * RD + k] = dv.x0[o] + dl;
+            else sPos[a * RF + k] = dv.gs0[(size_t)ii * RF + k] + fl;
         }
-        if (cfg.kick2 || cfg.kick1_drift) {
+        if (do_kick) dv.v[o] = v;
+    }
+    if (cfg.thermo || cfg.fire_red) {
+        for (int a = threadIdx.x; a < APB; a += NT) {
+            if (base + a >= dv.N) continue;
+            acc[R_E] += (double)sE[a];
+            acc[R_W] += (double)sW[a];
+            if (cfg.fire_red) {
+                double f2 = 0.0;
 #pragma unroll
-            for (int k = 0; k < D; ++k) dv.v[(size_t)k * Np + i] = v[k];
+                for (int k = 0; k < D; ++k) f2 += (double)sF[a * D + k] * (double)sF[a * D + k];
+                acc[R_FMAX2] = fmax(acc[R_FMAX2], f2);
+                if (!(f2 < INFINITY)) acc[R_BAD] = 1.0;
+            }
         }
     }
+    __syncthreads();
 
-    if (cfg.thermo || cfg.fire_red || cfg.kick1_drift) {
+    // ---- phase C: rows out, trigger
+    if (cfg.kick1_drift) {
+        if (!FP64P) {
+            float *go = dv.gs[cfg.out_buf];
+            for (int t = threadIdx.x; t < APB * RF; t += NT) {
+                const int a = t / RF, c = t - a * RF, ii = base + a;
+                if (ii >= dv.N) continue;
+                go[(size_t)ii * RF + c] = c < D ? sPos[a * RF + c] : dv.gs0[(size_t)ii * RF + c];
+            }
+        } else {
+            for (int a = threadIdx.x; a < APB; a += NT)
+                if (base + a < dv.N) dv.gd[cfg.out_buf][(size_t)(base + a) * RD + D] = 0.5 * dv.sigma[base + a];
+        }
+        float m = 0.f;
+        for (int a = threadIdx.x; a < APB; a += NT) m = fmaxf(m, sD2[a]);
+        trigger_fold(dv, m, false, cfg.cond_rebuild);
+    }
+    if (cfg.thermo || cfg.fire_red) {
         const bool last = block_reduce_and_fold<NT>(dv, acc, R_BAD + 1, dv.maxblocks, sh);
-        if (last && threadIdx.x == 0) {
+        if (last && threadIdx.x == 0 && cfg.fire_red) {
             const double *red = dv.red;
-            if (red[R_BAD] != 0.0) atomicOr(&dv.flags->error, (int)ERR_LOST);
-            if (cfg.kick1_drift) {
-                const double dmax2 = red[R_DMAX2];
-                const int trig = (4.0 * dmax2 > dv.skin * dv.skin) || red[R_BAD] != 0.0;
-                if (16.0 * dmax2 > dv.L * dv.L) atomicOr(&dv.flags->error, (int)ERR_LOST);
-                dv.flags->rebuild = trig;
-                if (cfg.cond_rebuild) cudaGraphSetConditional(cfg.cond_rebuild, trig ? 1u : 0u);
-            }
-            if (cfg.fire_red) {
-                // FIRE 2.0 scalar update (Guenole et al. 2020), one thread
-                double *fs = dv.flags->fire;
-                const double fmx = sqrt(red[R_FMAX2]);
-                fs[FS_FMAX] = fmx;
-                fs[FS_E] = 0.5 * red[R_E];
-                int status = FIRE_RUNNING;
-                if (red[R_BAD] != 0.0) status = FIRE_NEGFAIL;
-                else if (fmx < fs[FP_FTOL]) status = FIRE_CONVERGED;
-                else if (fmx < fs[FP_SWITCH]) status = FIRE_SWITCH;
-                else if (fs[FS_ITER] >= fs[FP_MAXITER]) status = FIRE_MAXITER;
-                else {
-                    double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
-                    const double P = red[R_P];
-                    if (P > 0.0) {
-                        fs[FS_NPOS] += 1.0;
-                        fs[FS_NNEG] = 0.0;
-                        if (fs[FS_NPOS] > fs[FP_NDELAY]) {
-                            dt = fmin(dt * fs[FP_FINC], fs[FP_DTMAX]);
-                            alpha *= fs[FP_FALPHA];
-                        }
-                        fs[FS_BRANCH] = 1.0;
-                        // |v + dt F/m| expanded over the sums of this reduction
-                        fs[FS_VNORM] = sqrt(fmax(red[R_VV] + 2.0 * dt * red[R_VF] + dt * dt * red[R_FF], 0.0));
-                        fs[FS_FNORM] = sqrt(red[R_FN]);
-                    } else {
-                        fs[FS_NPOS] = 0.0;
-                        fs[FS_NNEG] += 1.0;
-                        if (fs[FS_NNEG] > fs[FP_NNEGMAX]) status = FIRE_NEGFAIL;
-                        if (!(fs[FP_INITDELAY] != 0.0 && fs[FS_ITER] < fs[FP_NDELAY])) {
-                            dt = fmax(dt * fs[FP_FDEC], fs[FP_DTMIN]);
-                            alpha = fs[FP_ALPHA0];
-                        }
-                        fs[FS_BRANCH] = 0.0;
+            // FIRE 2.0 scalar update (Guenole et al. 2020), one thread
+            double *fs = dv.flags->fire;
+            const double fmx = sqrt(red[R_FMAX2]);
+            fs[FS_FMAX] = fmx;
+            fs[FS_E] = 0.5 * red[R_E];
+            int status = FIRE_RUNNING;
+            if (red[R_BAD] != 0.0) status = FIRE_NEGFAIL;
+            else if (fmx < fs[FP_FTOL]) status = FIRE_CONVERGED;
+            else if (fmx < fs[FP_SWITCH]) status = FIRE_SWITCH;
+            else if (fs[FS_ITER] >= fs[FP_MAXITER]) status = FIRE_MAXITER;
+            else {
+                double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
+                const double P = red[R_P];
+                if (P > 0.0) {
+                    fs[FS_NPOS] += 1.0;
+                    fs[FS_NNEG] = 0.0;
+                    if (fs[FS_NPOS] > fs[FP_NDELAY]) {
+                        dt = fmin(dt * fs[FP_FINC], fs[FP_DTMAX]);
+                        alpha *= fs[FP_FALPHA];
                     }
-                    fs[FS_DT] = dt;
-                    fs[FS_ALPHA] = alpha;
-                    if (status == FIRE_RUNNING) {
-                        fs[FS_ITER] += 1.0;
-                        fs[FS_PHASE_ITER] += 1.0;
+                    fs[FS_BRANCH] = 1.0;
+                    // |v + dt F/m| expanded over the sums of this reduction
+                    fs[FS_VNORM] = sqrt(fmax(red[R_VV] + 2.0 * dt * red[R_VF] + dt * dt * red[R_FF], 0.0));
+                    fs[FS_FNORM] = sqrt(red[R_FN]);
+                } else {
+                    fs[FS_NPOS] = 0.0;
+                    fs[FS_NNEG] += 1.0;
+                    if (fs[FS_NNEG] > fs[FP_NNEGMAX]) status = FIRE_NEGFAIL;
+                    if (!(fs[FP_INITDELAY] != 0.0 && fs[FS_ITER] < fs[FP_NDELAY])) {
+                        dt = fmax(dt * fs[FP_FDEC], fs[FP_DTMIN]);
+                        alpha = fs[FP_ALPHA0];
                     }
+                    fs[FS_BRANCH] = 0.0;
                 }
-                fs[FS_STATUS] = (double)status;
-                if (cfg.cond_loop) cudaGraphSetConditional(cfg.cond_loop, status == FIRE_RUNNING ? 1u : 0u);
+                fs[FS_DT] = dt;
+                fs[FS_ALPHA] = alpha;
+                if (status == FIRE_RUNNING) {
+                    fs[FS_ITER] += 1.0;
+                    fs[FS_PHASE_ITER] += 1.0;
+                }
             }
+            fs[FS_STATUS] = (double)status;
+            if (cfg.cond_loop) cudaGraphSetConditional(cfg.cond_loop, status == FIRE_RUNNING ? 1u : 0u);
         }
     }
 }
@@ -286,62 +320,59 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
 // FIRE per-atom update, from the scalars the last force reduction left:
 //   P <= 0 branch: x -= dt v / 2, v = 0;
 //   v += dt F/m;  P > 0 branch: v = (1-alpha) v + alpha |v| F/|F|;  x += dt v.
+// Block = NT/4 atoms; (axis, atom) items over all threads as in k_step.
 template <int D>
 __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
                                                     unsigned long long cond_rebuild) {
     constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
-    __shared__ double sh[(NT / 32) * kNRed];
+    constexpr int APB = NT / 4;
+    __shared__ float sPos[APB * RF];
+    __shared__ float sD2[APB];
     const double *fs = dv.flags->fire;
     if (fs[FS_STATUS] != (double)FIRE_RUNNING) return;
     const double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
     const bool up = fs[FS_BRANCH] != 0.0;
     const double vn = fs[FS_VNORM], fn = fs[FS_FNORM];
-    const int i = blockIdx.x * NT + threadIdx.x;
-    double acc[kNRed];
-#pragma unroll
-    for (int r = 0; r < kNRed; ++r) acc[r] = 0.0;
-    if (i < dv.N) {
-        const int Np = dv.Npad;
-        const double im = dv.inv_mass ? dv.inv_mass[i] : 1.0;
-        const bool mix = up && fn > 0.0;
-        const double cf = mix ? alpha * vn / fn : 0.0;
-        double d2 = 0.0;
-        bool bad = false;
-        float *go = dv.gs[0] + (size_t)i * RF;
-        const float *g0 = dv.gs0 + (size_t)i * RF;
-        double *gdo = dv.gd[0] + (size_t)i * RD;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const size_t o = (size_t)k * Np + i;
-            double v = dv.v[o], dl = dv.dlt[o];
-            const double F = dv.F[o];
-            if (!up) {
-                dl -= 0.5 * dt * v;
-                v = 0.0;
-            }
-            v += dt * F * im;
-            if (mix) v = (1.0 - alpha) * v + cf * F;
-            dl += dt * v;
-            dv.v[o] = v;
-            dv.dlt[o] = dl;
-            d2 += dl * dl;
-            go[k] = g0[k] + (float)dl;
-            if (write_fp64_rows) gdo[k] = dv.x0[o] + dl;
-            bad |= !(fabs(dl) < INFINITY);
+    const bool mix = up && fn > 0.0;
+    const double cf = mix ? alpha * vn / fn : 0.0;
+    const int base = blockIdx.x * APB;
+    const int Np = dv.Npad;
+    for (int a = threadIdx.x; a < APB; a += NT) sD2[a] = 0.f;
+    __syncthreads();
+    for (int t = threadIdx.x; t < APB * D; t += NT) {
+        const int k = t / APB, a = t - k * APB, ii = base + a;
+        if (ii >= dv.N) continue;
+        const size_t o = (size_t)k * Np + ii;
+        const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
+        double v = dv.v[o], dl = dv.dlt[o];
+        const double F = dv.F[o];
+        if (!up) {
+            dl -= 0.5 * dt * v;
+            v = 0.0;
         }
-        go[D] = g0[D];
-        if (write_fp64_rows) gdo[D] = 0.5 * dv.sigma[i];
-        acc[R_DMAX2] = d2;
-        if (bad) acc[R_BAD] = 1.0;
+        v += dt * F * im;
+        if (mix) v = (1.0 - alpha) * v + cf * F;
+        dl += dt * v;
+        dv.v[o] = v;
+        dv.dlt[o] = dl;
+        const float fl = (float)dl;
+        atomicAdd(&sD2[a], fl * fl);
+        sPos[a * RF + k] = dv.gs0[(size_t)ii * RF + k] + fl;
+        if (write_fp64_rows) dv.gd[0][(size_t)ii * RD + k] = dv.x0[o] + dl;
     }
-    const bool last = block_reduce_and_fold<NT>(dv, acc, R_BAD + 1, dv.maxblocks, sh);
-    if (last && threadIdx.x == 0) {
-        const double dmax2 = dv.red[R_DMAX2];
-        const int trig = (4.0 * dmax2 > dv.skin * dv.skin) || dv.red[R_BAD] != 0.0;
-        if (dv.red[R_BAD] != 0.0 || 16.0 * dmax2 > dv.L * dv.L) atomicOr(&dv.flags->error, (int)ERR_LOST);
-        dv.flags->rebuild = trig;
-        if (cond_rebuild) cudaGraphSetConditional(cond_rebuild, trig ? 1u : 0u);
+    __syncthreads();
+    float *go = dv.gs[0];
+    for (int t = threadIdx.x; t < APB * RF; t += NT) {
+        const int a = t / RF, c = t - a * RF, ii = base + a;
+        if (ii >= dv.N) continue;
+        go[(size_t)ii * RF + c] = c < D ? sPos[a * RF + c] : dv.gs0[(size_t)ii * RF + c];
     }
+    if (write_fp64_rows)
+        for (int a = threadIdx.x; a < APB; a += NT)
+            if (base + a < dv.N) dv.gd[0][(size_t)(base + a) * RD + D] = 0.5 * dv.sigma[base + a];
+    float m = 0.f;
+    for (int a = threadIdx.x; a < APB; a += NT) m = fmaxf(m, sD2[a]);
+    trigger_fold(dv, m, false, cond_rebuild);
 }
 
 // write gather rows of buffer buf from x0 + dlt (FP32 and/or FP64 rows)
@@ -370,11 +401,11 @@ void rows_impl(const Dev &dv, int buf, int w32, int w64, cudaStream_t s) {
 
 template <int D>
 void step_impl(const Dev &dv, const StepCfg &cfg, cudaStream_t s) {
-    const int64_t threads = (int64_t)dv.N * (cfg.compute_force ? dv.G : 1);
     const int G = cfg.compute_force ? dv.G : 1;
     Dev d2 = dv;
     d2.G = G;   // without a force loop the lanes of a group have nothing to share
-    const int blocks = (int)((threads + NT - 1) / NT);
+    const int apb = NT / G;
+    const int blocks = (dv.N + apb - 1) / apb;
     if (cfg.fp64_pairs)
         k_step<D, true><<<blocks, NT, 0, s>>>(cfg.compute_force ? dv : d2, cfg);
     else
@@ -383,7 +414,7 @@ void step_impl(const Dev &dv, const StepCfg &cfg, cudaStream_t s) {
 
 template <int D>
 void fire_update_impl(const Dev &dv, int w64, unsigned long long cond, cudaStream_t s) {
-    k_fire_update<D><<<(dv.N + NT - 1) / NT, NT, 0, s>>>(dv, w64, cond);
+    k_fire_update<D><<<(dv.N + NT / 4 - 1) / (NT / 4), NT, 0, s>>>(dv, w64, cond);
 }
 
 }  // namespace

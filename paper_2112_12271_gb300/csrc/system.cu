@@ -861,6 +861,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     dv.Lsc_f = (float)dv.Lsc;
     dv.L_f = (float)L;
     dv.halfL_f = (float)(0.5 * L);
+    dv.hmax_f = (float)(0.5 * smax);
 
     auto bail = [&](hdmd_status st) {
         destroy_system(sys);
@@ -876,7 +877,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     DA2(dv.gs0, Np * RF); DA2(dv.gs[0], Np * RF); DA2(dv.gs[1], Np * RF);
     DA2(dv.gd[0], Np * RD); DA2(dv.gd[1], Np * RD);
     DA2(dv.cell_count, dv.ncells); DA2(dv.cell_fill, dv.ncells); DA2(dv.cell_start, dv.ncells + 1);
-    DA2(dv.cell_of, Np); DA2(dv.perm, Np); DA2(dv.cellid, Np);
+    DA2(dv.cell_of, Np); DA2(dv.perm, Np); DA2(dv.cellid, Np); DA2(dv.batch_start, dv.ncells + 1);
     DA2(dv.tx, nd); DA2(dv.tv, nd); DA2(dv.tsig, Np); DA2(dv.tim, Np);
     DA2(dv.timg, nd); DA2(dv.tid, Np);
     DA2(dv.nnbr, Np);
@@ -1207,6 +1208,56 @@ hdmd_status swap_sweep(hdmd_system *sys, int nsweeps, double T, double p, uint64
     }
     // diameters changed: the list radii and the rows' sigma/2 are stale
     return build_forced(sys, sys->buf);
+}
+
+hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_out) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!ms_out || reps < 1 || reps > 100000 || !(dt > 0.0))
+        return fail(sys, HDMD_E_INVALID, "profile_kernels: bad arguments");
+    const bool fp64 = sys->prec == HDMD_FP64;
+    st = ensure_rows(sys, sys->buf, !fp64, fp64);
+    if (st) return st;
+    if (!sys->F_valid) {
+        st = force_only(sys, sys->buf, fp64, false);
+        if (st) return st;
+        sys->F_valid = true;
+    }
+    st = snapshot(sys, false);
+    if (st) return st;
+    const int buf0 = sys->buf;
+    std::vector<cudaEvent_t> ev(2 * reps);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    auto timed = [&](auto launch) -> double {
+        for (int r = 0; r < reps; ++r) {
+            cudaEventRecord(ev[2 * r], sys->stream);
+            launch(r);
+            cudaEventRecord(ev[2 * r + 1], sys->stream);
+        }
+        cudaStreamSynchronize(sys->stream);
+        double tot = 0.0;
+        for (int r = 0; r < reps; ++r) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+            tot += ms;
+        }
+        return tot / reps;
+    };
+    int cur = buf0;
+    ms_out[0] = timed([&](int) {
+        StepCfg c = base_cfg(sys, dt);
+        c.compute_force = 1; c.kick2 = 1; c.kick1_drift = 1;
+        c.in_buf = cur; c.out_buf = 1 - cur;
+        launch_step(sys->dv, c, sys->stream);
+        cur = 1 - cur;
+    });
+    ms_out[1] = timed([&](int) { launch_rebuild(sys->dv, cur, false, sys->stream); });
+    ms_out[2] = timed([&](int) { force_only(sys, cur, fp64, false); });
+    for (auto &e : ev) cudaEventDestroy(e);
+    CKL(sys);
+    st = snapshot(sys, true);
+    if (st) return st;
+    return build_forced(sys, buf0);
 }
 
 hdmd_status get_info(hdmd_system *sys, hdmd_info *info) {

@@ -90,6 +90,7 @@ def lib():
             "get_info": [vp, vp],
             "set_tuning": [vp, i32, i32],
             "destroy_system": [vp],
+            "profile_kernels": [vp, i32, dbl, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -230,6 +231,13 @@ def set_tuning(h, lanes_per_atom=0, use_graphs=-1):
     _check(lib().set_tuning(h, int(lanes_per_atom), int(use_graphs)), h)
 
 
+def profile_kernels(h, reps=50, dt=0.005):
+    """Average device ms of (fused MD kernel, full list build, force-only kernel)."""
+    out = np.zeros(3)
+    _check(lib().profile_kernels(h, int(reps), float(dt), _p(out)), h)
+    return dict(step_ms=out[0], rebuild_ms=out[1], force_ms=out[2])
+
+
 def destroy_system(h):
     if h:
         _check(lib().destroy_system(h))
@@ -280,6 +288,9 @@ class System:
 
     def tune(self, lanes_per_atom=0, use_graphs=-1):
         set_tuning(self.h, lanes_per_atom, use_graphs)
+
+    def profile(self, reps=50, dt=0.005):
+        return profile_kernels(self.h, reps, dt)
 
     def close(self):
         if self.h:
