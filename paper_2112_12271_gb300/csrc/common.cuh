@@ -30,6 +30,8 @@ namespace hdmd {
 
 constexpr int kMaxD = 10;
 constexpr int kNRed = 16;          // reduction slots per block
+constexpr int kStepNT = 128;       // threads per block of the force / update kernels
+constexpr int kMaxLanes = 32;      // largest lanes-per-atom group
 
 // reduction slots
 enum Red {

@@ -27,7 +27,7 @@
 namespace hdmd {
 namespace {
 
-constexpr int NT = 128;   // one wave of blocks at the benchmark size
+constexpr int NT = kStepNT;   // one wave of blocks at the benchmark size
 
 // Displacement trigger, shared by the MD and FIRE update kernels: every
 // block folds its max |dlt|^2 (float bits: non-negative floats order as

@@ -881,7 +881,8 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     DA2(dv.tx, nd); DA2(dv.tv, nd); DA2(dv.tsig, Np); DA2(dv.tim, Np);
     DA2(dv.timg, nd); DA2(dv.tid, Np);
     DA2(dv.nnbr, Np);
-    dv.maxblocks = (int)((Np * 32 + 255) / 256);
+    // most blocks any reducing kernel launches: kMaxLanes lanes per atom, kStepNT threads
+    dv.maxblocks = (int)((Np * kMaxLanes + kStepNT - 1) / kStepNT);
     DA2(dv.partials, (size_t)kNRed * dv.maxblocks);
     DA2(dv.red, kNRed);
     DA2(dv.flags, 1);
