@@ -194,6 +194,34 @@ hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs);
  * lists) is restored before returning. */
 hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_out);
 
+/* Forces, pair energy and virial of N harmonic spheres, for callers that
+ * cannot allocate GPU memory when they need them: code running while a CUDA
+ * graph is captured (allocation cannot be captured), plug-ins inside a host
+ * framework whose memory pool owns the device, loops that forbid allocation
+ * after start-up.  The paper has no counterpart of this call; it is the FP64
+ * force kernel with all pairs in place of the Verlet list, so it needs no
+ * system handle, no list and no cell arrays.
+ * Arguments: d in 2..10; N atoms, at most 524288; box side L (which must be
+ * at least twice the largest diameter, not checked); device pointers x_dev
+ * [N*d] row-major positions, sigma_dev [N] diameters, F_dev [N*d] forces out,
+ * ew_dev [2] out (pair energy, virial); eps as in hdmd_potential; cuda_stream
+ * a cudaStream_t (NULL = legacy default stream).  The call is asynchronous:
+ * the outputs are ready when the stream reaches it.
+ * Memory: it allocates nothing.  Its only scratch is a file-scope device
+ * array of 65,792 bytes that every GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (once per device, with the device current), so make the first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (the call clears what must start at zero), so
+ * calls that overlap on the GPU, on any streams, race: serialise them.
+ * Errors: HDMD_E_UNSUPPORTED_D, HDMD_E_INVALID (N above the limit, NULL
+ * buffer, bad L or eps), HDMD_E_CUDA; hdmd_noalloc_last_error() gives the
+ * reason. */
+hdmd_status compute_forces_noalloc(int d, int64_t N, double L, const double *x_dev,
+                                   const double *sigma_dev, double eps, double *F_dev,
+                                   double *ew_dev, void *cuda_stream);
+const char *hdmd_noalloc_last_error(void);
+
 /* Free everything the system holds.  NULL is accepted. */
 hdmd_status destroy_system(hdmd_system *sys);
 

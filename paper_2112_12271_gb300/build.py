@@ -19,7 +19,8 @@ OBJ = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIB_DIR, "libhdmd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["kernels_bin.cu", "kernels_nbr.cu", "kernels_force.cu", "kernels_swap.cu", "system.cu"]
+UNITS = ["kernels_bin.cu", "kernels_nbr.cu", "kernels_force.cu", "kernels_swap.cu", "system.cu",
+         "noalloc.cu"]
 
 
 def nvcc() -> str:
