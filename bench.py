@@ -202,6 +202,8 @@ def run_gpu(args):
                     stream=stream.cuda_stream)
     if args.eager:
         g.tune(use_graphs=0)   # profilers cannot see kernels inside conditional graphs
+    if args.lanes:
+        g.tune(lanes_per_atom=args.lanes)
     info = g.info()
     if ws > 1:
         torch.distributed.barrier()
@@ -308,6 +310,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per atom (0: library default)")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu)")
     args = ap.parse_args()

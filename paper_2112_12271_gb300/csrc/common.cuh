@@ -78,6 +78,7 @@ struct Flags {
 
 struct Dev {
     int d, N, Npad, G, cap;
+    int lgG;        // log2(G)
     double L, halfL, invL, skin, eps;
     int n;          // subcells per axis
     int ncells;
@@ -113,8 +114,9 @@ template <int D> struct Rows {
 
 __host__ __device__ inline int pow_int(int b, int e) { int r = 1; for (int k = 0; k < e; ++k) r *= b; return r; }
 
-__device__ __forceinline__ int64_t list_pos(int m, int i, int Npad, int G) {
-    return ((int64_t)(m / G) * Npad + i) * G + (m % G);
+// entry m of atom i (G = 1 << lgG lanes per atom)
+__device__ __forceinline__ int64_t list_pos(int m, int i, int Npad, int lgG) {
+    return (((int64_t)(m >> lgG) * Npad + i) << lgG) + (m & ((1 << lgG) - 1));
 }
 
 // Deterministic grid reduction.  Each block reduces its threads' nslots

@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
     __shared__ float sPos[FP64P ? 1 : NT * RF];
     __shared__ int sBad;
     if (cfg.fire_red && dv.flags->fire[FS_STATUS] != (double)FIRE_RUNNING) return;  // loop ended
-    const int G = dv.G, APB = NT / G;
-    const int al = threadIdx.x / G, g = threadIdx.x - al * G;
+    const int G = dv.G, lgG = dv.lgG, APB = NT >> lgG;
+    const int al = threadIdx.x >> lgG, g = threadIdx.x & (G - 1);
     const int base = blockIdx.x * APB;
     const int i = base + al;
     const bool valid = i < dv.N;
@@ -100,8 +100,10 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
 #pragma unroll
                 for (int k = 0; k < D; ++k) xi[k] = ri[k];
                 const double hi = ri[D];
-                for (int m = g; m < nn; m += G) {
-                    const int j = dv.nbr[list_pos(m, i, Np, G)];
+                const int64_t lstride = (int64_t)Np << lgG;
+                int64_t pos = ((int64_t)i << lgG) + g;
+                for (int m = g; m < nn; m += G, pos += lstride) {
+                    const int j = dv.nbr[pos];
                     const double *rj = dv.gd[cfg.in_buf] + (size_t)j * RD;
                     double dx[D], r2 = 0.0;
 #pragma unroll
@@ -131,14 +133,15 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
                 const float Lsc = dv.Lsc_f;
                 const float eps = (float)dv.eps;
                 constexpr int U = 4;   // list entries in flight per lane
-                for (int m0 = g; m0 < nn; m0 += U * G) {
+                const int64_t lstride = (int64_t)Np << lgG;
+                int64_t pos0 = ((int64_t)i << lgG) + g;
+                for (int m0 = g; m0 < nn; m0 += U * G, pos0 += U * lstride) {
                     int jv[U];
                     uint32_t cv[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int m = m0 + u * G;
-                        const bool ok = m < nn;
-                        const int64_t pos = list_pos(ok ? m : g, i, Np, G);
+                        const bool ok = m0 + u * G < nn;
+                        const int64_t pos = pos0 + u * lstride;
                         jv[u] = ok ? dv.nbr[pos] : -1;
                         cv[u] = ok ? dv.code[pos] : 0u;
                     }
@@ -404,6 +407,7 @@ void step_impl(const Dev &dv, const StepCfg &cfg, cudaStream_t s) {
     const int G = cfg.compute_force ? dv.G : 1;
     Dev d2 = dv;
     d2.G = G;   // without a force loop the lanes of a group have nothing to share
+    d2.lgG = cfg.compute_force ? dv.lgG : 0;
     const int apb = NT / G;
     const int blocks = (dv.N + apb - 1) / apb;
     if (cfg.fp64_pairs)

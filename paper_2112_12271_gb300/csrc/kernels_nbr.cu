@@ -74,110 +74,96 @@ __global__ void __launch_bounds__(NT, 4) k_nbr_build(Dev dv, bool guarded) {
         cnt[h] = 0;
     }
     const float reach_pad = dv.hmax_f;   // largest candidate radius
-    // lane h (< nh) keeps its own home atom for the row-reach test
-    float xmine[D];
-    float reach2_mine = -1.f;
-    {
-        const int i = lane < nh ? h0 + lane : h0;
-        const float *ri = dv.gs0 + (size_t)i * RF;
-#pragma unroll
-        for (int k = 0; k < D; ++k) xmine[k] = ri[k];
-        const float reach = (ri[D] + skin + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
-        if (lane < nh) reach2_mine = reach * reach;
-    }
-
     const int base = WRAP ? 3 : 2;
     const int Srow = pow_int(base, D - 1);
-    int Jstride = 1;   // n^(D-1) is not needed: rows differ in axes 0..D-2
-    (void)Jstride;
     const int cl = C[D - 1];
-    for (int sr = 0; sr < Srow; ++sr) {
-        // offsets of axes 0..D-2 from the base-3 (or base-2) digits of sr
-        int off[D];
-        {
+    const int cl_m = cl == 0 ? n - 1 : cl - 1, cl_p = cl == n - 1 ? 0 : cl + 1;
+    const unsigned allh = (1u << nh) - 1u;
+
+    // rows of the stencil, 32 at a time: lane l works out row sr0 + l (its
+    // subcell index, offset code and which home atoms can reach it), then
+    // the warp walks the reachable rows one by one
+    for (int sr0 = 0; sr0 < Srow; sr0 += 32) {
+        const int sr = sr0 + lane;
+        int Jrow = 0;
+        uint32_t rcode = 0;
+        unsigned amask = 0;
+        if (sr < Srow) {
+            int off[D];
             int rem = sr;
 #pragma unroll
             for (int k = D - 2; k >= 0; --k) { off[k] = rem % base - (WRAP ? 1 : 0); rem /= base; }
-        }
-        int Jrow = 0;   // linear index of the row's subcell with last coordinate 0
-#pragma unroll
-        for (int k = 0; k < D - 1; ++k) {
-            int cj = C[k] + off[k];
-            cj = cj < 0 ? cj + n : (cj >= n ? cj - n : cj);
-            Jrow = Jrow * n + cj;
-        }
-        Jrow *= n;
-        // which home atoms can reach this row
-        unsigned active;
-        if (WRAP) {
-            float b2 = 0.f;
 #pragma unroll
             for (int k = 0; k < D - 1; ++k) {
-                float dk = off[k] > 0 ? hLsc - xmine[k] : (off[k] < 0 ? xmine[k] + hLsc : 0.f);
-                dk = fmaxf(dk, 0.f);
-                b2 = fmaf(dk, dk, b2);
+                int cj = C[k] + off[k];
+                cj = cj < 0 ? cj + n : (cj >= n ? cj - n : cj);
+                Jrow = Jrow * n + cj;
+                rcode |= (uint32_t)(off[k] + 1) << (2 * k);
             }
-            active = __ballot_sync(0xffffffffu, b2 < reach2_mine) & ((1u << H) - 1u);
-        } else {
-            active = (1u << nh) - 1u;
-        }
-        if (!active) continue;
-        uint32_t rowcode = 0;
+            Jrow *= n;
+            if (WRAP) {
 #pragma unroll
-        for (int k = 0; k < D - 1; ++k) rowcode |= (uint32_t)(off[k] + 1) << (2 * k);
-        // candidate ranges of the row: up to two contiguous pieces
-        int ra0, ra1, rb0 = 0, rb1 = 0;
-        if (WRAP) {
-            const int cm = cl - 1, cp = cl + 1;
-            if (cm >= 0 && cp < n) {
-                ra0 = dv.cell_start[Jrow + cm];
-                ra1 = dv.cell_start[Jrow + cp + 1];
-            } else if (cm < 0) {   // cells 0, 1 then n-1
-                ra0 = dv.cell_start[Jrow];
-                ra1 = dv.cell_start[Jrow + min(cp, n - 1) + 1];
-                rb0 = dv.cell_start[Jrow + n - 1];
-                rb1 = dv.cell_start[Jrow + n];
-                if (n - 1 <= cp) rb0 = rb1;   // n == 2 cannot occur here (n >= 3)
-            } else {               // cells n-2, n-1 then 0
-                ra0 = dv.cell_start[Jrow + cm];
-                ra1 = dv.cell_start[Jrow + n];
-                rb0 = dv.cell_start[Jrow];
-                rb1 = dv.cell_start[Jrow + 1];
-            }
-        } else {
-            ra0 = dv.cell_start[Jrow];
-            ra1 = dv.cell_start[Jrow + 2];
-        }
-        for (int piece = 0; piece < 2; ++piece) {
-            const int p0 = piece ? rb0 : ra0, p1 = piece ? rb1 : ra1;
-            for (int b0 = p0; b0 < p1; b0 += 32) {
-                const int j = b0 + lane;
-                const bool okj = j < p1;
-                const int jj = okj ? j : p0;
-                // last-axis subcell of the candidate -> its offset
-                int olast;
-                {
-                    const int cjl = dv.cellid[jj] - Jrow;   // 0..n-1
-                    int o = cjl - cl;
-                    if (WRAP) o = o > 1 ? o - n : (o < -1 ? o + n : o);
-                    else o = o != 0 ? 1 : 0;
-                    olast = o;
+                for (int h = 0; h < H; ++h) {
+                    float b2 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D - 1; ++k) {
+                        float dk = off[k] > 0 ? hLsc - xh[h][k] : (off[k] < 0 ? xh[h][k] + hLsc : 0.f);
+                        dk = fmaxf(dk, 0.f);
+                        b2 = fmaf(dk, dk, b2);
+                    }
+                    const float reach = (rh[h] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
+                    if (b2 < reach * reach) amask |= 1u << h;
                 }
+                amask &= allh;
+            } else {
+                amask = allh;
+            }
+        }
+        unsigned rows = __ballot_sync(0xffffffffu, amask != 0);
+        while (rows) {
+            const int src = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const int Jr = __shfl_sync(0xffffffffu, Jrow, src);
+            const uint32_t rc0 = __shfl_sync(0xffffffffu, rcode, src);
+            const unsigned active = __shfl_sync(0xffffffffu, amask, src);
+            float offL[D];   // offsets of axes 0..D-2 times L_sc (WRAP)
+#pragma unroll
+            for (int k = 0; k < D - 1; ++k) offL[k] = (float)((int)((rc0 >> (2 * k)) & 3u) - 1) * Lsc;
+            // the row's subcells along the last axis, as up to three pieces
+            int s1, l1, s2, l2, s3 = 0, l3 = 0;
+            int o1, o2, o3 = 1;
+            if (WRAP) {
+                s1 = dv.cell_start[Jr + cl_m]; l1 = dv.cell_start[Jr + cl_m + 1] - s1; o1 = -1;
+                s2 = dv.cell_start[Jr + cl];   l2 = dv.cell_start[Jr + cl + 1] - s2;   o2 = 0;
+                s3 = dv.cell_start[Jr + cl_p]; l3 = dv.cell_start[Jr + cl_p + 1] - s3; o3 = 1;
+            } else {
+                s1 = dv.cell_start[Jr + cl];     l1 = dv.cell_start[Jr + cl + 1] - s1;     o1 = 0;
+                s2 = dv.cell_start[Jr + 1 - cl]; l2 = dv.cell_start[Jr + 2 - cl] - s2; o2 = 1;
+            }
+            const int tot = l1 + l2 + l3;
+            for (int t0 = 0; t0 < tot; t0 += 32) {
+                const int t = t0 + lane;
+                const bool okj = t < tot;
+                int j, olast;
+                if (t < l1) { j = s1 + t; olast = o1; }
+                else if (t < l1 + l2) { j = s2 + (t - l1); olast = o2; }
+                else { j = s3 + (t - l1 - l2); olast = o3; }
+                if (!okj) { j = s1 < dv.N ? s1 : 0; olast = o1; }
                 float rj[RF];
                 {
-                    const float4 *rj4 = reinterpret_cast<const float4 *>(dv.gs0 + (size_t)jj * RF);
+                    const float4 *rj4 = reinterpret_cast<const float4 *>(dv.gs0 + (size_t)j * RF);
 #pragma unroll
                     for (int q = 0; q < RF / 4; ++q) {
-                        const float4 t = __ldg(rj4 + q);
-                        rj[4 * q] = t.x; rj[4 * q + 1] = t.y; rj[4 * q + 2] = t.z; rj[4 * q + 3] = t.w;
+                        const float4 tt = __ldg(rj4 + q);
+                        rj[4 * q] = tt.x; rj[4 * q + 1] = tt.y; rj[4 * q + 2] = tt.z; rj[4 * q + 3] = tt.w;
                     }
                 }
                 if (WRAP) {
 #pragma unroll
-                    for (int k = 0; k < D - 1; ++k) rj[k] = fmaf((float)off[k], Lsc, rj[k]);
+                    for (int k = 0; k < D - 1; ++k) rj[k] += offL[k];
                     rj[D - 1] = fmaf((float)olast, Lsc, rj[D - 1]);
                 }
-                const uint32_t wcode = WRAP ? (rowcode | ((uint32_t)(olast + 1) << (2 * (D - 1)))) : 0u;
+                const uint32_t wcode = WRAP ? (rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)))) : 0u;
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
                     if (!(active & (1u << h))) continue;   // warp-uniform
@@ -196,7 +182,7 @@ __global__ void __launch_bounds__(NT, 4) k_nbr_build(Dev dv, bool guarded) {
                             code = 0u;
 #pragma unroll
                             for (int k = 0; k < D; ++k) {
-                                const int ok = k < D - 1 ? off[k] : olast;   // 0 or +1
+                                const int ok = k < D - 1 ? (int)((rc0 >> (2 * k)) & 3u) - 1 : olast;   // 0 or +1
                                 float dx = rj[k] - xh[h][k];
                                 int o = ok;
                                 if (ok) {
@@ -216,14 +202,14 @@ __global__ void __launch_bounds__(NT, 4) k_nbr_build(Dev dv, bool guarded) {
                             hit = false;
                         } else if (fabsf(diff) <= band) {
                             // FP64 decision (positions are x0 at a build)
-                            double s2 = 0.0;
+                            double s2d = 0.0;
                             for (int k = 0; k < D; ++k) {
                                 double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
                                 dx -= dv.L * rint(dx * dv.invL);
-                                s2 += dx * dx;
+                                s2d += dx * dx;
                             }
                             const double rcd = 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
-                            hit = s2 < rcd * rcd;
+                            hit = s2d < rcd * rcd;
                         } else {
                             hit = diff < 0.f;
                         }
@@ -233,7 +219,7 @@ __global__ void __launch_bounds__(NT, 4) k_nbr_build(Dev dv, bool guarded) {
                     if (hit) {
                         const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
                         if (idx < dv.cap) {
-                            const int64_t pos = list_pos(idx, i, dv.Npad, dv.G);
+                            const int64_t pos = list_pos(idx, i, dv.Npad, dv.lgG);
                             dv.nbr[pos] = j;
                             dv.code[pos] = code;
                         }

@@ -848,6 +848,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     dv.N = (int)N;
     dv.Npad = (int)((N + 63) / 64 * 64);
     dv.G = default_lanes(N);
+    dv.lgG = __builtin_ctz(dv.G);
     dv.L = L;
     dv.halfL = 0.5 * L;
     dv.invL = 1.0 / L;
@@ -1287,6 +1288,7 @@ hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs) {
         if (lanes_per_atom < 1 || lanes_per_atom > 32 || (lanes_per_atom & (lanes_per_atom - 1)))
             return fail(sys, HDMD_E_INVALID, "lanes_per_atom must be a power of two in 1..32");
         sys->dv.G = lanes_per_atom;
+        sys->dv.lgG = __builtin_ctz(lanes_per_atom);
         hdmd_status st = alloc_lists(sys, sys->dv.cap);
         if (st) return st;
     }
