@@ -30,28 +30,39 @@ namespace {
 constexpr int NT = kStepNT;   // one wave of blocks at the benchmark size
 
 // Displacement trigger, shared by the MD and FIRE update kernels: every
-// block folds its max |dlt|^2 (float bits: non-negative floats order as
-// unsigned integers, NaN above all) into flags->disp_bits; the last block
-// (ticket, no waiting) turns it into the rebuild flag and, inside a CUDA
-// graph, into the IF condition, then clears the word for the next launch.
+// block stores its max |dlt|^2 (float bits: non-negative floats order as
+// unsigned integers, NaN above all) in a word of its own; the last block
+// (ticket, no waiting) takes the maximum over all blocks and turns it into
+// the rebuild flag and, inside a CUDA graph, into the IF condition.
 __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bool blk_bad,
                                              unsigned long long cond) {
     __shared__ bool last;
-    unsigned bits = __float_as_uint(blk_max_d2);
-    bits = __reduce_max_sync(0xffffffffu, bits);
-    if ((threadIdx.x & 31) == 0 && bits) atomicMax(&dv.flags->disp_bits, bits);
-    if (blk_bad && (threadIdx.x & 31) == 0) atomicOr(&dv.flags->error, (int)ERR_LOST);
-    __threadfence();
+    __shared__ unsigned wmax[32];
+    unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(blk_max_d2));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
+    if (blk_bad) atomicOr(&dv.flags->error, (int)ERR_LOST);
     __syncthreads();
+    unsigned *part = reinterpret_cast<unsigned *>(dv.partials);   // one word per block
     if (threadIdx.x == 0) {
-        unsigned t = atomicAdd(&dv.flags->counter, 1u);
+        unsigned b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, wmax[w]);
+        part[blockIdx.x] = b;
+        __threadfence();
+        const unsigned t = atomicAdd(&dv.flags->counter, 1u);
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const unsigned b = atomicExch(&dv.flags->disp_bits, 0u);
-        const float d2 = __uint_as_float(b);
+    if (!last) return;
+    __threadfence();
+    unsigned b = 0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) b = max(b, __ldcg(part + k));
+    b = __reduce_max_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
+        const float d2 = __uint_as_float(m);
         const float s2 = (float)(dv.skin * dv.skin) * (1.0f - 1e-5f);
         const bool finite = d2 <= 3.0e38f;
         const int trig = (4.0f * d2 > s2) || !finite;
