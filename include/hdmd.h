@@ -222,6 +222,66 @@ hdmd_status compute_forces_noalloc(int d, int64_t N, double L, const double *x_d
                                    double *ew_dev, void *cuda_stream);
 const char *hdmd_noalloc_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Batched jobs: many independent systems of uneven N and d advanced by one
+ * persistent kernel per dimension (one thread block per job at a time), for
+ * throughput on many small systems and for the serving loop.  Each job runs
+ * the same method as a single system (lists over the 3^d subcells, pair
+ * forces, FIRE 2.0 or velocity Verlet) with unit masses.
+ * ---------------------------------------------------------------------- */
+typedef struct hdmd_batch hdmd_batch;
+
+typedef struct {
+    int kind;             /* 0: MD (nsteps of velocity Verlet, step dt), 1: FIRE */
+    int d;                /* 2..10 */
+    int64_t N;
+    double L, eps, skin;
+    double dt;            /* MD */
+    int64_t nsteps;       /* MD */
+    int list_capacity;    /* 0: estimated from the density */
+    hdmd_fire_params fire;/* FIRE; dt0 <= 0 takes the defaults of fire_minimize */
+} hdmd_job_spec;
+
+typedef struct {
+    int status;           /* 0 running, 1 done, 2 FIRE stopped unconverged, 3 error */
+    int kind;
+    int64_t iterations;   /* FIRE iterations or MD steps done */
+    int64_t rebuilds;
+    double E_pair, virial, K, fmax;
+    int converged;        /* FIRE: max_i |F_i| < f_tol */
+    int error;            /* 1: list overflow (re-admit with a larger list_capacity), 2: lost atom */
+} hdmd_job_result;
+
+/* A batch with a device pool of pool_bytes (cudaMalloc once) and room for
+ * max_jobs jobs; prec as for create_system; kernels run on cuda_stream. */
+hdmd_status batch_create(int64_t pool_bytes, int max_jobs, hdmd_precision prec,
+                         void *cuda_stream, hdmd_batch **out);
+/* Admit one job: diameters[N], positions x[N*d] (row-major, host), velocities
+ * v[N*d] (nullable).  Its memory is carved out of the pool; HDMD_E_NOMEM when
+ * the pool (or the job table) has no room now: remove finished jobs first.
+ * *job_id receives the job's slot. */
+hdmd_status batch_add(hdmd_batch *b, const hdmd_job_spec *spec, const double *diameters,
+                      const double *x, const double *v, int *job_id);
+/* One launch over every running job: each advances by at most budget FIRE
+ * iterations or MD steps (0: until it finishes).  *n_unfinished (nullable)
+ * receives the number still running.  Synchronises the stream. */
+hdmd_status batch_run(hdmd_batch *b, int64_t budget, int *n_unfinished);
+/* Result of a job (finished or not); x (nullable, host [N*d]) receives its
+ * positions wrapped into the box, in the caller's atom order. */
+hdmd_status batch_result(hdmd_batch *b, int job_id, hdmd_job_result *res, double *x);
+/* Return a job's memory to the pool and free its slot. */
+hdmd_status batch_remove(hdmd_batch *b, int job_id);
+/* Free pool bytes, live jobs, lanes per atom by dimension (int[11]); nullable. */
+hdmd_status batch_info(hdmd_batch *b, int64_t *free_bytes, int *live_jobs, int *lanes_by_d);
+/* Autotuner of the block shape per dimension: times the force evaluation of
+ * each dimension's median job with 1..16 lanes per atom (reps evaluations,
+ * CUDA events) and keeps the fastest for that dimension. */
+hdmd_status batch_autotune(hdmd_batch *b, int reps);
+/* Set the lanes per atom (power of two, 1..16) of a dimension by hand. */
+hdmd_status batch_set_lanes(hdmd_batch *b, int d, int lanes);
+hdmd_status batch_destroy(hdmd_batch *b);
+const char *hdmd_batch_last_error(const hdmd_batch *b);
+
 /* Free everything the system holds.  NULL is accepted. */
 hdmd_status destroy_system(hdmd_system *sys);
 

@@ -19,8 +19,9 @@ OBJ = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIB_DIR, "libhdmd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["kernels_bin.cu", "kernels_nbr.cu", "kernels_force.cu", "kernels_swap.cu", "system.cu",
-         "noalloc.cu"]
+UNITS = ["kernels_bin.cu", "kernels_nbr.cu", "kernels_force.cu", "kernels_swap.cu",
+         "kernels_batch_lo.cu", "kernels_batch_d6.cu", "kernels_batch_d8.cu", "system.cu",
+         "batch.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

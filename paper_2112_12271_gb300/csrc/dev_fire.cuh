@@ -1,0 +1,57 @@
+// dev_fire.cuh -- the FIRE 2.0 scalar update (Guenole et al., Comput. Mater.
+// Sci. 175, 109584 (2020); Sec. II.B of the paper names the method), run by one
+// thread after the force reduction of an iteration.  fs holds the state and
+// parameters (FireSlot indices), red the reduced sums (Red indices) of the
+// forces and velocities at the current positions.  Order of tests: converged
+// (max_i |F_i| < f_tol), precision switch, max_iter; then the P = F.v rules.
+// Writes and returns the new status.
+#pragma once
+#include "common.cuh"
+
+namespace hdmd {
+
+__device__ __forceinline__ int fire_scalar_update(double *fs, const double *red) {
+    const double fmx = sqrt(red[R_FMAX2]);
+    fs[FS_FMAX] = fmx;
+    fs[FS_E] = 0.5 * red[R_E];
+    int status = FIRE_RUNNING;
+    if (red[R_BAD] != 0.0) status = FIRE_NEGFAIL;
+    else if (fmx < fs[FP_FTOL]) status = FIRE_CONVERGED;
+    else if (fmx < fs[FP_SWITCH]) status = FIRE_SWITCH;
+    else if (fs[FS_ITER] >= fs[FP_MAXITER]) status = FIRE_MAXITER;
+    else {
+        double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
+        const double P = red[R_P];
+        if (P > 0.0) {
+            fs[FS_NPOS] += 1.0;
+            fs[FS_NNEG] = 0.0;
+            if (fs[FS_NPOS] > fs[FP_NDELAY]) {
+                dt = fmin(dt * fs[FP_FINC], fs[FP_DTMAX]);
+                alpha *= fs[FP_FALPHA];
+            }
+            fs[FS_BRANCH] = 1.0;
+            // |v + dt F/m| expanded over the sums of this reduction
+            fs[FS_VNORM] = sqrt(fmax(red[R_VV] + 2.0 * dt * red[R_VF] + dt * dt * red[R_FF], 0.0));
+            fs[FS_FNORM] = sqrt(red[R_FN]);
+        } else {
+            fs[FS_NPOS] = 0.0;
+            fs[FS_NNEG] += 1.0;
+            if (fs[FS_NNEG] > fs[FP_NNEGMAX]) status = FIRE_NEGFAIL;
+            if (!(fs[FP_INITDELAY] != 0.0 && fs[FS_ITER] < fs[FP_NDELAY])) {
+                dt = fmax(dt * fs[FP_FDEC], fs[FP_DTMIN]);
+                alpha = fs[FP_ALPHA0];
+            }
+            fs[FS_BRANCH] = 0.0;
+        }
+        fs[FS_DT] = dt;
+        fs[FS_ALPHA] = alpha;
+        if (status == FIRE_RUNNING) {
+            fs[FS_ITER] += 1.0;
+            fs[FS_PHASE_ITER] += 1.0;
+        }
+    }
+    fs[FS_STATUS] = (double)status;
+    return status;
+}
+
+}  // namespace hdmd

@@ -1,0 +1,118 @@
+// dev_force.cuh -- the pair force / energy / virial loop over one atom's
+// Verlet list, shared by the grid kernels (kernels_force.cu) and the batched
+// kernel (kernels_batch.cu).  Harmonic spheres: U = (eps/2)(1 - r/s_ij)^2 for
+// r < s_ij; force on i = (eps/s_ij)(1 - r/s_ij)(x_i - x_j)/r.
+// Lane g of the atom's group of G = 1 << lgG lanes walks entries g, g+G, ...
+// and accumulates its share into f, e (sum of U) and w (sum of r.f); the
+// caller combines the lanes.  FP64P selects FP64 pair arithmetic on the
+// absolute FP64 rows (minimum image by rint) or FP32 arithmetic on the
+// cell-relative FP32 rows with the entry's subcell-offset code.
+#pragma once
+#include "common.cuh"
+
+#ifndef HDMD_FORCE_UNROLL
+#define HDMD_FORCE_UNROLL 3
+#endif
+
+namespace hdmd {
+
+template <int D, bool FP64P, typename FT>
+__device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG, int in_buf,
+                                            FT (&f)[D], FT &e, FT &w) {
+    constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
+    const int G = 1 << lgG;
+    const int Np = dv.Npad;
+    const int nn = dv.nnbr[i];
+    if (FP64P) {
+        const double *ri = dv.gd[in_buf] + (size_t)i * RD;
+        double xi[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xi[k] = ri[k];
+        const double hi = ri[D];
+        const int64_t lstride = (int64_t)Np << lgG;
+        int64_t pos = ((int64_t)i << lgG) + g;
+        for (int m = g; m < nn; m += G, pos += lstride) {
+            const int j = dv.nbr[pos];
+            const double *rj = dv.gd[in_buf] + (size_t)j * RD;
+            double dx[D], r2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double t = xi[k] - rj[k];
+                t -= dv.L * rint(t * dv.invL);
+                dx[k] = t;
+                r2 += t * t;
+            }
+            const double s = hi + rj[D];
+            if (r2 < s * s) {
+                const double r = sqrt(r2);
+                const double gg = 1.0 - r / s;
+                const double fr = r > 0.0 ? (dv.eps / s) * gg / r : 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) f[k] += (FT)(fr * dx[k]);
+                e += (FT)(0.5 * dv.eps * gg * gg);
+                w += (FT)(fr * r2);
+            }
+        }
+    } else {
+        const float *ri = dv.gs[in_buf] + (size_t)i * RF;
+        float xi[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xi[k] = ri[k];
+        const float hi = ri[D];
+        const float Lsc = dv.Lsc_f;
+        const float eps = (float)dv.eps;
+        constexpr int U = HDMD_FORCE_UNROLL;   // list entries in flight per lane
+        const int64_t lstride = (int64_t)Np << lgG;
+        int64_t pos0 = ((int64_t)i << lgG) + g;
+        for (int m0 = g; m0 < nn; m0 += U * G, pos0 += U * lstride) {
+            int jv[U];
+            uint32_t cv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = m0 + u * G < nn;
+                const int64_t pos = pos0 + u * lstride;
+                jv[u] = ok ? dv.nbr[pos] : -1;
+                cv[u] = ok ? dv.code[pos] : 0u;
+            }
+            float rj[U][RF];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float4 *rj4 = reinterpret_cast<const float4 *>(
+                    dv.gs[in_buf] + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF);
+#pragma unroll
+                for (int q = 0; q < RF / 4; ++q) {
+                    const float4 t = __ldg(rj4 + q);
+                    rj[u][4 * q] = t.x; rj[u][4 * q + 1] = t.y;
+                    rj[u][4 * q + 2] = t.z; rj[u][4 * q + 3] = t.w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (jv[u] < 0) continue;
+                const uint32_t code = cv[u];
+                float dx[D], r2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float o = (float)((int)((code >> (2 * k)) & 3u) - 1);
+                    const float t = fmaf(-o, Lsc, xi[k] - rj[u][k]);
+                    dx[k] = t;
+                    r2 = fmaf(t, t, r2);
+                }
+                const float s = hi + rj[u][D];
+                if (r2 < s * s && r2 > 0.f) {
+                    const float inv_s = __frcp_rn(s);
+                    const float rinv = rsqrtf(r2);
+                    const float r = r2 * rinv;
+                    const float gg = fmaf(-r, inv_s, 1.f);
+                    const float fr = eps * inv_s * gg * rinv;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+                    e = (FT)fmaf(0.5f * eps * gg, gg, (float)e);
+                    w = (FT)fmaf(fr, r2, (float)w);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace hdmd

@@ -1,0 +1,216 @@
+// dev_nbr.cuh -- device function of the Verlet-list build (see
+// kernels_nbr.cu for the method); shared by the grid and batched kernels.
+#pragma once
+#include "common.cuh"
+
+namespace hdmd {
+
+// Lists of home batch w (one warp; lane = 0..31).  Called by the grid
+// kernel below (one warp per batch) and by the batched-job kernel (the warps
+// of one block loop over the batches of one job).
+template <int D, bool WRAP>
+__device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
+    constexpr int RF = Rows<D>::RF;
+    constexpr int H = home_batch(D);
+    // home subcell: largest c with batch_start[c] <= w
+    int lo = 0, hi = dv.ncells - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (dv.batch_start[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int c = lo;
+    const int cs = dv.cell_start[c], ce = dv.cell_start[c + 1];
+    const int h0 = cs + (w - dv.batch_start[c]) * H;
+    const int nh = min(H, ce - h0);
+    const int n = dv.n;
+    int C[D];
+    {
+        int t = c;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) { C[k] = t % n; t /= n; }
+    }
+    const float Lsc = dv.Lsc_f, hLsc = 0.5f * dv.Lsc_f, hL = dv.halfL_f;
+    const float skin = (float)dv.skin;
+    const float band_abs = 1e-5f * Lsc * Lsc;
+
+    // home atoms in registers (identical in every lane)
+    float xh[H][D], rh[H];
+    int cnt[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int i = h < nh ? h0 + h : h0;
+        const float *ri = dv.gs0 + (size_t)i * RF;
+#pragma unroll
+        for (int k = 0; k < D; ++k) xh[h][k] = ri[k];
+        rh[h] = ri[D] + skin;
+        cnt[h] = 0;
+    }
+    const float reach_pad = dv.hmax_f;   // largest candidate radius
+    const int base = WRAP ? 3 : 2;
+    const int Srow = pow_int(base, D - 1);
+    const int cl = C[D - 1];
+    const int cl_m = cl == 0 ? n - 1 : cl - 1, cl_p = cl == n - 1 ? 0 : cl + 1;
+    const unsigned allh = (1u << nh) - 1u;
+
+    // rows of the stencil, 32 at a time: lane l works out row sr0 + l (its
+    // subcell index, offset code and which home atoms can reach it), then
+    // the warp walks the reachable rows one by one
+    for (int sr0 = 0; sr0 < Srow; sr0 += 32) {
+        const int sr = sr0 + lane;
+        int Jrow = 0;
+        uint32_t rcode = 0;
+        unsigned amask = 0;
+        if (sr < Srow) {
+            int off[D];
+            int rem = sr;
+#pragma unroll
+            for (int k = D - 2; k >= 0; --k) { off[k] = rem % base - (WRAP ? 1 : 0); rem /= base; }
+#pragma unroll
+            for (int k = 0; k < D - 1; ++k) {
+                int cj = C[k] + off[k];
+                cj = cj < 0 ? cj + n : (cj >= n ? cj - n : cj);
+                Jrow = Jrow * n + cj;
+                rcode |= (uint32_t)(off[k] + 1) << (2 * k);
+            }
+            Jrow *= n;
+            if (WRAP) {
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    float b2 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D - 1; ++k) {
+                        float dk = off[k] > 0 ? hLsc - xh[h][k] : (off[k] < 0 ? xh[h][k] + hLsc : 0.f);
+                        dk = fmaxf(dk, 0.f);
+                        b2 = fmaf(dk, dk, b2);
+                    }
+                    const float reach = (rh[h] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
+                    if (b2 < reach * reach) amask |= 1u << h;
+                }
+                amask &= allh;
+            } else {
+                amask = allh;
+            }
+        }
+        unsigned rows = __ballot_sync(0xffffffffu, amask != 0);
+        while (rows) {
+            const int src = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const int Jr = __shfl_sync(0xffffffffu, Jrow, src);
+            const uint32_t rc0 = __shfl_sync(0xffffffffu, rcode, src);
+            const unsigned active = __shfl_sync(0xffffffffu, amask, src);
+            float offL[D];   // offsets of axes 0..D-2 times L_sc (WRAP)
+#pragma unroll
+            for (int k = 0; k < D - 1; ++k) offL[k] = (float)((int)((rc0 >> (2 * k)) & 3u) - 1) * Lsc;
+            // the row's subcells along the last axis, as up to three pieces
+            int s1, l1, s2, l2, s3 = 0, l3 = 0;
+            int o1, o2, o3 = 1;
+            if (WRAP) {
+                s1 = dv.cell_start[Jr + cl_m]; l1 = dv.cell_start[Jr + cl_m + 1] - s1; o1 = -1;
+                s2 = dv.cell_start[Jr + cl];   l2 = dv.cell_start[Jr + cl + 1] - s2;   o2 = 0;
+                s3 = dv.cell_start[Jr + cl_p]; l3 = dv.cell_start[Jr + cl_p + 1] - s3; o3 = 1;
+            } else {
+                s1 = dv.cell_start[Jr + cl];     l1 = dv.cell_start[Jr + cl + 1] - s1;     o1 = 0;
+                s2 = dv.cell_start[Jr + 1 - cl]; l2 = dv.cell_start[Jr + 2 - cl] - s2; o2 = 1;
+            }
+            const int tot = l1 + l2 + l3;
+            for (int t0 = 0; t0 < tot; t0 += 32) {
+                const int t = t0 + lane;
+                const bool okj = t < tot;
+                int j, olast;
+                if (t < l1) { j = s1 + t; olast = o1; }
+                else if (t < l1 + l2) { j = s2 + (t - l1); olast = o2; }
+                else { j = s3 + (t - l1 - l2); olast = o3; }
+                if (!okj) { j = s1 < dv.N ? s1 : 0; olast = o1; }
+                float rj[RF];
+                {
+                    const float4 *rj4 = reinterpret_cast<const float4 *>(dv.gs0 + (size_t)j * RF);
+#pragma unroll
+                    for (int q = 0; q < RF / 4; ++q) {
+                        const float4 tt = __ldg(rj4 + q);
+                        rj[4 * q] = tt.x; rj[4 * q + 1] = tt.y; rj[4 * q + 2] = tt.z; rj[4 * q + 3] = tt.w;
+                    }
+                }
+                if (WRAP) {
+#pragma unroll
+                    for (int k = 0; k < D - 1; ++k) rj[k] += offL[k];
+                    rj[D - 1] = fmaf((float)olast, Lsc, rj[D - 1]);
+                }
+                const uint32_t wcode = WRAP ? (rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)))) : 0u;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    if (!(active & (1u << h))) continue;   // warp-uniform
+                    const int i = h0 + h;
+                    bool hit = false;
+                    uint32_t code = wcode;
+                    if (okj && j != i) {
+                        float r2 = 0.f;
+                        if (WRAP) {
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                const float dx = rj[k] - xh[h][k];
+                                r2 = fmaf(dx, dx, r2);
+                            }
+                        } else {
+                            code = 0u;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                const int ok = k < D - 1 ? (int)((rc0 >> (2 * k)) & 3u) - 1 : olast;   // 0 or +1
+                                float dx = rj[k] - xh[h][k];
+                                int o = ok;
+                                if (ok) {
+                                    const float dp = (rj[k] + Lsc) - xh[h][k];
+                                    if (dp > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
+                                    else dx = dp;
+                                }
+                                code |= (uint32_t)(o + 1) << (2 * k);
+                                r2 = fmaf(dx, dx, r2);
+                            }
+                        }
+                        const float rc = rh[h] + rj[D];
+                        const float rc2 = rc * rc;
+                        const float diff = r2 - rc2;
+                        const float band = band_abs + 1e-5f * rc2;
+                        if (diff > band) {
+                            hit = false;
+                        } else if (fabsf(diff) <= band) {
+                            // FP64 decision (positions are x0 at a build)
+                            double s2d = 0.0;
+                            for (int k = 0; k < D; ++k) {
+                                double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
+                                dx -= dv.L * rint(dx * dv.invL);
+                                s2d += dx * dx;
+                            }
+                            const double rcd = 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                            hit = s2d < rcd * rcd;
+                        } else {
+                            hit = diff < 0.f;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (!m) continue;
+                    if (hit) {
+                        const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
+                        if (idx < dv.cap) {
+                            const int64_t pos = list_pos(idx, i, dv.Npad, dv.lgG);
+                            dv.nbr[pos] = j;
+                            dv.code[pos] = code;
+                        }
+                    }
+                    cnt[h] += __popc(m);
+                }
+            }
+        }
+    }
+    if (lane < nh) {
+        int cnt_l = 0;
+#pragma unroll
+        for (int h = 0; h < H; ++h) if (h == lane) cnt_l = cnt[h];
+        const int i = h0 + lane;
+        dv.nnbr[i] = min(cnt_l, dv.cap);
+        if (cnt_l > dv.cap) atomicOr(&dv.flags->error, (int)ERR_OVERFLOW);
+        atomicMax(&dv.flags->max_count, cnt_l);
+        atomicAdd((unsigned long long *)&dv.flags->total_entries, (unsigned long long)cnt_l);
+    }
+}
+
+}  // namespace hdmd

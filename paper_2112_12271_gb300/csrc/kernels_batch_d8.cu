@@ -1,0 +1,8 @@
+// kernels_batch_d8.cu -- batched-job kernels for d = 8..10 (see batch_impl.cuh).
+#include "batch_impl.cuh"
+
+namespace hdmd {
+HDMD_BATCH_INSTANTIATE(8)
+HDMD_BATCH_INSTANTIATE(9)
+HDMD_BATCH_INSTANTIATE(10)
+}  // namespace hdmd

@@ -22,6 +22,12 @@
 // of x_n and writing those of x_{n+1} into the other buffer.
 #include <type_traits>
 
+#include "dev_fire.cuh"
+#include "dev_force.cuh"
+
+#ifndef HDMD_STEP_MIN_BLOCKS
+#define HDMD_STEP_MIN_BLOCKS 8
+#endif
 #include "launch.h"
 
 namespace hdmd {
@@ -80,7 +86,7 @@ __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bo
 // runs with every lane busy and every SoA access coalesced.  Phase C writes
 // the new gather rows (contiguous for the block) and folds the trigger.
 template <int D, bool FP64P>
-__global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
+__global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepCfg cfg) {
     using FT = typename std::conditional<FP64P, double, float>::type;
     constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
     __shared__ double sh[(NT / 32) * kNRed];
@@ -103,99 +109,7 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
 #pragma unroll
         for (int k = 0; k < D; ++k) f[k] = 0;
         FT e = 0, w = 0;
-        if (valid) {
-            const int nn = dv.nnbr[i];
-            if (FP64P) {
-                const double *ri = dv.gd[cfg.in_buf] + (size_t)i * RD;
-                double xi[D];
-#pragma unroll
-                for (int k = 0; k < D; ++k) xi[k] = ri[k];
-                const double hi = ri[D];
-                const int64_t lstride = (int64_t)Np << lgG;
-                int64_t pos = ((int64_t)i << lgG) + g;
-                for (int m = g; m < nn; m += G, pos += lstride) {
-                    const int j = dv.nbr[pos];
-                    const double *rj = dv.gd[cfg.in_buf] + (size_t)j * RD;
-                    double dx[D], r2 = 0.0;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        double t = xi[k] - rj[k];
-                        t -= dv.L * rint(t * dv.invL);
-                        dx[k] = t;
-                        r2 += t * t;
-                    }
-                    const double s = hi + rj[D];
-                    if (r2 < s * s) {
-                        const double r = sqrt(r2);
-                        const double gg = 1.0 - r / s;
-                        const double fr = r > 0.0 ? (dv.eps / s) * gg / r : 0.0;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) f[k] += (FT)(fr * dx[k]);
-                        e += (FT)(0.5 * dv.eps * gg * gg);
-                        w += (FT)(fr * r2);
-                    }
-                }
-            } else {
-                const float *ri = dv.gs[cfg.in_buf] + (size_t)i * RF;
-                float xi[D];
-#pragma unroll
-                for (int k = 0; k < D; ++k) xi[k] = ri[k];
-                const float hi = ri[D];
-                const float Lsc = dv.Lsc_f;
-                const float eps = (float)dv.eps;
-                constexpr int U = 4;   // list entries in flight per lane
-                const int64_t lstride = (int64_t)Np << lgG;
-                int64_t pos0 = ((int64_t)i << lgG) + g;
-                for (int m0 = g; m0 < nn; m0 += U * G, pos0 += U * lstride) {
-                    int jv[U];
-                    uint32_t cv[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const bool ok = m0 + u * G < nn;
-                        const int64_t pos = pos0 + u * lstride;
-                        jv[u] = ok ? dv.nbr[pos] : -1;
-                        cv[u] = ok ? dv.code[pos] : 0u;
-                    }
-                    float rj[U][RF];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const float4 *rj4 = reinterpret_cast<const float4 *>(
-                            dv.gs[cfg.in_buf] + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF);
-#pragma unroll
-                        for (int q = 0; q < RF / 4; ++q) {
-                            const float4 t = __ldg(rj4 + q);
-                            rj[u][4 * q] = t.x; rj[u][4 * q + 1] = t.y;
-                            rj[u][4 * q + 2] = t.z; rj[u][4 * q + 3] = t.w;
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if (jv[u] < 0) continue;
-                        const uint32_t code = cv[u];
-                        float dx[D], r2 = 0.f;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            const float o = (float)((int)((code >> (2 * k)) & 3u) - 1);
-                            const float t = fmaf(-o, Lsc, xi[k] - rj[u][k]);
-                            dx[k] = t;
-                            r2 = fmaf(t, t, r2);
-                        }
-                        const float s = hi + rj[u][D];
-                        if (r2 < s * s && r2 > 0.f) {
-                            const float inv_s = __frcp_rn(s);
-                            const float rinv = rsqrtf(r2);
-                            const float r = r2 * rinv;
-                            const float gg = fmaf(-r, inv_s, 1.f);
-                            const float fr = eps * inv_s * gg * rinv;
-#pragma unroll
-                            for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
-                            e = (FT)fmaf(0.5f * eps * gg, gg, (float)e);
-                            w = (FT)fmaf(fr, r2, (float)w);
-                        }
-                    }
-                }
-            }
-        }
+        if (valid) pair_forces<D, FP64P, FT>(dv, i, g, lgG, cfg.in_buf, f, e, w);
         for (int o = G >> 1; o > 0; o >>= 1) {
 #pragma unroll
             for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
@@ -286,46 +200,7 @@ __global__ void __launch_bounds__(NT) k_step(Dev dv, StepCfg cfg) {
             const double *red = dv.red;
             // FIRE 2.0 scalar update (Guenole et al. 2020), one thread
             double *fs = dv.flags->fire;
-            const double fmx = sqrt(red[R_FMAX2]);
-            fs[FS_FMAX] = fmx;
-            fs[FS_E] = 0.5 * red[R_E];
-            int status = FIRE_RUNNING;
-            if (red[R_BAD] != 0.0) status = FIRE_NEGFAIL;
-            else if (fmx < fs[FP_FTOL]) status = FIRE_CONVERGED;
-            else if (fmx < fs[FP_SWITCH]) status = FIRE_SWITCH;
-            else if (fs[FS_ITER] >= fs[FP_MAXITER]) status = FIRE_MAXITER;
-            else {
-                double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
-                const double P = red[R_P];
-                if (P > 0.0) {
-                    fs[FS_NPOS] += 1.0;
-                    fs[FS_NNEG] = 0.0;
-                    if (fs[FS_NPOS] > fs[FP_NDELAY]) {
-                        dt = fmin(dt * fs[FP_FINC], fs[FP_DTMAX]);
-                        alpha *= fs[FP_FALPHA];
-                    }
-                    fs[FS_BRANCH] = 1.0;
-                    // |v + dt F/m| expanded over the sums of this reduction
-                    fs[FS_VNORM] = sqrt(fmax(red[R_VV] + 2.0 * dt * red[R_VF] + dt * dt * red[R_FF], 0.0));
-                    fs[FS_FNORM] = sqrt(red[R_FN]);
-                } else {
-                    fs[FS_NPOS] = 0.0;
-                    fs[FS_NNEG] += 1.0;
-                    if (fs[FS_NNEG] > fs[FP_NNEGMAX]) status = FIRE_NEGFAIL;
-                    if (!(fs[FP_INITDELAY] != 0.0 && fs[FS_ITER] < fs[FP_NDELAY])) {
-                        dt = fmax(dt * fs[FP_FDEC], fs[FP_DTMIN]);
-                        alpha = fs[FP_ALPHA0];
-                    }
-                    fs[FS_BRANCH] = 0.0;
-                }
-                fs[FS_DT] = dt;
-                fs[FS_ALPHA] = alpha;
-                if (status == FIRE_RUNNING) {
-                    fs[FS_ITER] += 1.0;
-                    fs[FS_PHASE_ITER] += 1.0;
-                }
-            }
-            fs[FS_STATUS] = (double)status;
+            const int status = fire_scalar_update(fs, red);
             if (cfg.cond_loop) cudaGraphSetConditional(cfg.cond_loop, status == FIRE_RUNNING ? 1u : 0u);
         }
     }

@@ -60,6 +60,22 @@ class Info(C.Structure):
                 ("precision", C.c_int), ("graphs", C.c_int), ("device_bytes", C.c_int64)]
 
 
+class JobSpec(C.Structure):
+    _fields_ = [("kind", C.c_int), ("d", C.c_int), ("N", C.c_int64), ("L", C.c_double),
+                ("eps", C.c_double), ("skin", C.c_double), ("dt", C.c_double),
+                ("nsteps", C.c_int64), ("list_capacity", C.c_int), ("fire", FireParams)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("kind", C.c_int), ("iterations", C.c_int64),
+                ("rebuilds", C.c_int64), ("E_pair", C.c_double), ("virial", C.c_double),
+                ("K", C.c_double), ("fmax", C.c_double), ("converged", C.c_int),
+                ("error", C.c_int)]
+
+
+JOB_MD, JOB_FIRE = 0, 1
+JOB_RUNNING, JOB_DONE, JOB_NOT_CONVERGED, JOB_ERROR = 0, 1, 2, 3
+
 FIRE_DEFAULTS = dict(dt0=0.005, dt_max=0.05, dt_min=1e-4, f_inc=1.1, f_dec=0.5, alpha0=0.25,
                      f_alpha=0.99, f_tol=1e-10, polish_tol=1e-6, n_delay=20, n_neg_max=2000,
                      max_iter=1000000, initial_delay=1)
@@ -91,6 +107,15 @@ def lib():
             "set_tuning": [vp, i32, i32],
             "destroy_system": [vp],
             "profile_kernels": [vp, i32, dbl, vp],
+            "batch_create": [i64, i32, i32, vp, C.POINTER(vp)],
+            "batch_add": [vp, vp, vp, vp, vp, C.POINTER(i32)],
+            "batch_run": [vp, i64, C.POINTER(i32)],
+            "batch_result": [vp, i32, vp, vp],
+            "batch_remove": [vp, i32],
+            "batch_info": [vp, C.POINTER(i64), C.POINTER(i32), vp],
+            "batch_autotune": [vp, i32],
+            "batch_set_lanes": [vp, i32, i32],
+            "batch_destroy": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -98,6 +123,8 @@ def lib():
             f.restype = C.c_int
         L.hdmd_last_error.argtypes = [vp]
         L.hdmd_last_error.restype = C.c_char_p
+        L.hdmd_batch_last_error.argtypes = [vp]
+        L.hdmd_batch_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -295,6 +322,89 @@ class System:
     def close(self):
         if self.h:
             destroy_system(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batches
+def _bcheck(st, b=None):
+    if st != 0:
+        raise HDMDError(st, lib().hdmd_batch_last_error(b).decode(errors="replace"))
+
+
+class Batch:
+    """Many independent MD / FIRE jobs advanced by persistent kernels (batch_* ABI)."""
+
+    def __init__(self, pool_bytes=1 << 30, max_jobs=1024, precision=HDMD_MIXED, stream=None):
+        self.h = C.c_void_p()
+        _bcheck(lib().batch_create(int(pool_bytes), int(max_jobs), int(precision),
+                                   stream if stream is not None else default_stream(),
+                                   C.byref(self.h)))
+        self.meta = {}
+
+    def add(self, kind, d, L, diameters, x, v=None, eps=1.0, skin=0.3, dt=0.005, nsteps=0,
+            list_capacity=0, **fire):
+        diam = _f64(diameters)
+        N = diam.shape[0]
+        p = dict(FIRE_DEFAULTS)
+        p.update(fire)
+        spec = JobSpec(int(kind), int(d), int(N), float(L), float(eps), float(skin), float(dt),
+                       int(nsteps), int(list_capacity), FireParams(**p))
+        xx = _f64(x)
+        vv = None if v is None else _f64(v)
+        jid = C.c_int(-1)
+        st = lib().batch_add(self.h, C.byref(spec), _p(diam), _p(xx), _p(vv), C.byref(jid))
+        if st == 2:
+            return None          # no room now (pool or job table)
+        _bcheck(st, self.h)
+        self.meta[jid.value] = (N, int(d))
+        return jid.value
+
+    def run(self, budget=0):
+        left = C.c_int(0)
+        _bcheck(lib().batch_run(self.h, int(budget), C.byref(left)), self.h)
+        return left.value
+
+    def result(self, jid, positions=False):
+        r = JobResult()
+        N, d = self.meta[jid]
+        x = np.empty((N, d)) if positions else None
+        _bcheck(lib().batch_result(self.h, int(jid), C.byref(r), _p(x)), self.h)
+        out = {k: getattr(r, k) for k, _ in JobResult._fields_}
+        if positions:
+            out["x"] = x
+        return out
+
+    def remove(self, jid):
+        _bcheck(lib().batch_remove(self.h, int(jid)), self.h)
+        self.meta.pop(jid, None)
+
+    def info(self):
+        fb, lj = C.c_int64(0), C.c_int(0)
+        lanes = np.zeros(11, dtype=np.int32)
+        _bcheck(lib().batch_info(self.h, C.byref(fb), C.byref(lj), _p(lanes)), self.h)
+        return dict(free_bytes=fb.value, live_jobs=lj.value, lanes=lanes.tolist())
+
+    def autotune(self, reps=3):
+        _bcheck(lib().batch_autotune(self.h, int(reps)), self.h)
+
+    def set_lanes(self, d, lanes):
+        _bcheck(lib().batch_set_lanes(self.h, int(d), int(lanes)), self.h)
+
+    def close(self):
+        if self.h:
+            lib().batch_destroy(self.h)
             self.h = None
 
     def __enter__(self):
