@@ -39,7 +39,7 @@ UNIT = "atom-steps/s"
 WORKLOAD = "d6_N32768_polydisperse_harmonic_L6_NVE_dt0.005_skin0.3"
 # c1: the benchmark system; c1l: the same density with N = 2^21 (L = 12), whose
 # working set exceeds L2 (the HBM-bound case used for ncu captures)
-WORKLOADS = {"c1": 32768, "c1l": 2 ** 21}
+WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0}
 
 
 def dist_env():
@@ -298,6 +298,82 @@ def run_gpu(args):
     return 0
 
 
+# --------------------------------------------------------------------- batched FIRE
+def run_batch(args):
+    """512 independent FIRE minimisations (to max|F_i| < 1e-10) in the batched
+    engine, mixed precision with FP64 polish; compared with the plain FP64
+    single-system path run one job after another on a bounded sample."""
+    import torch
+    from paper_2112_12271_gb300 import build as B
+    from paper_2112_12271_gb300 import hdmd
+    torch.cuda.set_device(0)
+    B.build()
+    specs = W.c3_batch_specs(args.jobs, seed=0)
+    systems = [W.c3_job(sp) for sp in specs]
+    stream = torch.cuda.current_stream()
+    atoms = sum(sp["N"] for sp in specs)
+    pool = sum(2500 * sp["N"] * sp["d"] for sp in specs) + (256 << 20)
+
+    def one_pass():
+        b = hdmd.Batch(pool_bytes=pool, max_jobs=len(specs) + 8, precision=hdmd.HDMD_MIXED,
+                       stream=stream.cuda_stream)
+        ids = [b.add(hdmd.JOB_FIRE, s.d, s.L, s.sigma, s.x, max_iter=args.max_iter)
+               for s in systems]
+        assert all(i is not None for i in ids)
+        if args.autotune:
+            b.autotune(reps=2)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        c = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        left = b.run(0)
+        c.record(stream)
+        c.synchronize()
+        res = [b.result(i) for i in ids]
+        lanes = b.info()["lanes"]
+        b.close()
+        return a.elapsed_time(c), left, res, lanes
+
+    for _ in range(max(1, args.warmup - 2)):
+        one_pass()
+    times, res, lanes = [], None, None
+    for _ in range(args.steps):
+        ms, left, res, lanes = one_pass()
+        times.append(ms)
+    conv = sum(1 for r in res if r["converged"])
+    fmax = max(r["fmax"] for r in res if r["converged"]) if conv else None
+    iters = sum(r["iterations"] for r in res)
+    value = conv * args.steps / (sum(times) / 1000.0)   # converged jobs only
+    # plain FP64 single-system path, one job after another, bounded sample
+    sample = systems[:args.fp64_sample]
+    t0 = time.perf_counter()
+    fp64_conv = 0
+    for s in sample:
+        with hdmd.System(s.d, s.L, s.sigma, s.x, precision=hdmd.HDMD_FP64,
+                         stream=stream.cuda_stream) as g:
+            r = g.fire(max_iter=args.max_iter)
+            fp64_conv += int(r["converged"])
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    fp64_value = fp64_conv / t64
+    line = {"metric": "batched FIRE jobs/s converged to |F|max<1e-10 (512 jobs, d 3-6, N 256-8192)",
+            "value": value, "unit": "jobs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-pair/f64-accumulate+f64-polish", "data": "synthetic",
+            "config": {"workload": "batch_fire_512_d3-6_N256-8192_bidisperse",
+                       "jobs": len(specs), "atoms": atoms, "lanes_by_d": lanes[3:7],
+                       "autotuned": bool(args.autotune)},
+            "converged": conv, "stopped_at_max_iter": len(specs) - conv, "max_iter": args.max_iter,
+            "max_fmax_converged": fmax, "fire_iterations_total": iters,
+            "fp64_sequential": {"value": fp64_value, "unit": "converged jobs/s", "jobs": len(sample),
+                                "converged": fp64_conv,
+                                "sample": "first %d jobs, one System(FP64).fire() each" % len(sample)},
+            "speedup_vs_fp64_sequential": value / fp64_value}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,6 +387,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per atom (0: library default)")
+    ap.add_argument("--jobs", type=int, default=512, help="batched workload: number of jobs")
+    ap.add_argument("--fp64-sample", type=int, default=16,
+                    help="batched workload: jobs of the sequential FP64 comparison")
+    ap.add_argument("--autotune", type=int, default=1, help="batched workload: run the autotuner")
+    ap.add_argument("--max-iter", type=int, default=20000,
+                    help="batched workload: FIRE iteration limit per job")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu)")
     args = ap.parse_args()
@@ -318,6 +400,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

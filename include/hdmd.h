@@ -104,8 +104,9 @@ typedef struct {
 
 /* Create a system: d in 2..10 (else HDMD_E_UNSUPPORTED_D), N >= 2 atoms,
  * box side L, diameters[N] (host, > 0 and finite, copied).  Requires
- * L >= 2 (max sigma + skin) so that n_cell = floor(L/(max sigma + skin)) >= 2
- * (Eq. (7)) and minimum images are unique.  prec selects FP64 or mixed
+ * L > 2 max sigma, so that only one periodic image of a pair can interact.
+ * The subcells per axis are n_cell = floor(L/(max sigma + skin)) (Eq. (7));
+ * when that is 1 the lists are built over all pairs.  prec selects FP64 or mixed
  * (FP32 pair arithmetic; FP64 positions, velocities and reductions).
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
  * kernel of this system runs.  Positions start at the origin: call

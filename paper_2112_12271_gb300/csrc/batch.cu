@@ -255,8 +255,9 @@ hdmd_status batch_add(hdmd_batch *b, const hdmd_job_spec *spec, const double *di
     for (int64_t a = 0; a < N * d; ++a)
         if (!std::isfinite(x[a]) || (v && !std::isfinite(v[a])))
             return bfail(b, HDMD_E_INVALID, "non-finite position or velocity");
-    int n = (int)std::floor(spec->L / (smax + spec->skin));   // Eq. (7)
-    if (n < 2) return bfail(b, HDMD_E_INVALID, "box too small: L must be >= 2 (max diameter + skin)");
+    if (!(spec->L > 2.0 * smax))
+        return bfail(b, HDMD_E_INVALID, "box too small: L must exceed twice the largest diameter");
+    int n = std::max(1, (int)std::floor(spec->L / (smax + spec->skin)));   // Eq. (7)
     while (n > 2 && std::pow((double)n, d) > 8.0 * (double)N + 4096.0) --n;
     int id = -1;
     for (int k = 0; k < b->max_jobs; ++k)

@@ -46,7 +46,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
         cnt[h] = 0;
     }
     const float reach_pad = dv.hmax_f;   // largest candidate radius
-    const int base = WRAP ? 3 : 2;
+    const int base = WRAP ? 3 : (n == 1 ? 1 : 2);   // distinct offsets per axis
     const int Srow = pow_int(base, D - 1);
     const int cl = C[D - 1];
     const int cl_m = cl == 0 ? n - 1 : cl - 1, cl_p = cl == n - 1 ? 0 : cl + 1;
@@ -108,9 +108,12 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                 s1 = dv.cell_start[Jr + cl_m]; l1 = dv.cell_start[Jr + cl_m + 1] - s1; o1 = -1;
                 s2 = dv.cell_start[Jr + cl];   l2 = dv.cell_start[Jr + cl + 1] - s2;   o2 = 0;
                 s3 = dv.cell_start[Jr + cl_p]; l3 = dv.cell_start[Jr + cl_p + 1] - s3; o3 = 1;
-            } else {
+            } else if (n == 2) {
                 s1 = dv.cell_start[Jr + cl];     l1 = dv.cell_start[Jr + cl + 1] - s1;     o1 = 0;
                 s2 = dv.cell_start[Jr + 1 - cl]; l2 = dv.cell_start[Jr + 2 - cl] - s2; o2 = 1;
+            } else {   // one subcell: every atom
+                s1 = dv.cell_start[0]; l1 = dv.cell_start[1] - s1; o1 = 0;
+                s2 = s1; l2 = 0; o2 = 0;
             }
             const int tot = l1 + l2 + l3;
             for (int t0 = 0; t0 < tot; t0 += 32) {
@@ -161,6 +164,9 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                                     const float dp = (rj[k] + Lsc) - xh[h][k];
                                     if (dp > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
                                     else dx = dp;
+                                } else if (n == 1) {   // L_sc = L: nearest image either way
+                                    if (dx > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
+                                    else if (dx < -hL) { dx = (rj[k] + Lsc) - xh[h][k]; o = 1; }
                                 }
                                 code |= (uint32_t)(o + 1) << (2 * k);
                                 r2 = fmaf(dx, dx, r2);

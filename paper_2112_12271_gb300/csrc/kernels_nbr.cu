@@ -23,7 +23,9 @@
 // With n_cell = 2 the offsets -1 and +1 name the same subcell, so each
 // subcell is visited once (offsets {0, +1}) and every pair takes the minimum
 // image along the axes where the two subcells differ; the paper switches to
-// an all-pairs search there, which this amounts to.
+// an all-pairs search there, which this amounts to.  A box shorter than
+// 2 (sigma_max + s) (but longer than 2 sigma_max, so that only one image of a
+// pair can interact) has a single subcell: all pairs, minimum image per axis.
 #include "dev_nbr.cuh"
 #include "launch.h"
 

@@ -86,7 +86,7 @@ __global__ void k_swap_lists(Dev dv, SwapDev sw, int buf) {
     const float Lsc = dv.Lsc_f, hL = dv.halfL_f;
     const float R = (float)sw.rcut * (1.0f + 1e-5f) + 1e-5f;
     const float R2 = R * R;
-    const int base = WRAP ? 3 : 2;
+    const int base = WRAP ? 3 : (n == 1 ? 1 : 2);
     const int S = pow_int(base, D);
     int cnt = 0;
     int32_t *out = sw.slist + (size_t)w * sw.scap;
@@ -116,6 +116,9 @@ __global__ void k_swap_lists(Dev dv, SwapDev sw, int buf) {
                         if (off[k]) {
                             const float dp = (rb[k] + Lsc) - xa[k];
                             dx = dp > hL ? (rb[k] - Lsc) - xa[k] : dp;
+                        } else if (n == 1) {
+                            if (dx > hL) dx = (rb[k] - Lsc) - xa[k];
+                            else if (dx < -hL) dx = (rb[k] + Lsc) - xa[k];
                         }
                     }
                     r2 = fmaf(dx, dx, r2);

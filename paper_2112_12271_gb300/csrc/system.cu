@@ -826,10 +826,10 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
         smax = std::max(smax, diameters[i]);
     }
     const double rc = smax + pot->skin;
-    int n = (int)std::floor(L / rc);   // Eq. (7)
-    if (n < 2)
-        return fail(nullptr, HDMD_E_INVALID,
-                    "box too small: L must be >= 2 (max diameter + skin) so that n_cell >= 2");
+    // only one periodic image of a pair may interact: L > 2 max diameter
+    if (!(L > 2.0 * smax))
+        return fail(nullptr, HDMD_E_INVALID, "box too small: L must exceed twice the largest diameter");
+    int n = std::max(1, (int)std::floor(L / rc));   // Eq. (7); 1: a single subcell, all pairs
     // larger subcells stay exact; cap the subcell count at ~8N (+4096)
     const double cap_cells = 8.0 * (double)N + 4096.0;
     while (n > 2 && std::pow((double)n, d) > cap_cells) --n;

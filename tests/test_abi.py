@@ -49,7 +49,7 @@ def test_errors_without_gpu_are_reported_not_raised(libpath):
     assert st == 8   # HDMD_E_UNSUPPORTED_D
     assert b"d must be" in lib.hdmd_last_error(None)
     st = lib.create_system(3, 10, 2.0, diam.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
-    assert st == 1   # box too small for two subcells
+    assert st == 1   # box not longer than twice the largest diameter
     assert b"box too small" in lib.hdmd_last_error(None)
     bad = diam.copy(); bad[3] = -1.0
     st = lib.create_system(3, 10, 9.0, bad.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
