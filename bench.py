@@ -39,7 +39,7 @@ UNIT = "atom-steps/s"
 WORKLOAD = "d6_N32768_polydisperse_harmonic_L6_NVE_dt0.005_skin0.3"
 # c1: the benchmark system; c1l: the same density with N = 2^21 (L = 12), whose
 # working set exceeds L2 (the HBM-bound case used for ncu captures)
-WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0}
+WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0, "serve": 0}
 
 
 def dist_env():
@@ -373,6 +373,48 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     return 0
 
+# --------------------------------------------------------------------- serving
+def run_serve(args):
+    """Poisson stream (200 requests/s) of MD and FIRE requests through the
+    continuous-batching server; p50/p99 latency and jobs/s, beside the same
+    first requests served one after another as plain FP64 systems."""
+    from paper_2112_12271_gb300 import serve   # sets the stream work-queue count first
+    from paper_2112_12271_gb300 import build as B
+    from paper_2112_12271_gb300 import hdmd
+    import torch
+    torch.cuda.set_device(0)
+    B.build()
+    reqs = W.c4_requests(duration=args.serve_seconds, rate=200.0, seed=0)
+    systems = [W.c4_system(r) for r in reqs]
+    warm = W.c4_requests(duration=0.05, rate=200.0, seed=1)
+    warm_sys = [W.c4_system(r) for r in warm]
+    srv = serve.Server(precision=hdmd.HDMD_MIXED, slots=args.slots, small_N=args.small_n,
+                       batch_pool_bytes=args.pool_gb << 30, budget=args.budget)
+    srv.run(warm, warm_sys)            # warm-up: builds, graphs, allocator
+    recs = srv.run(reqs, systems, time_limit=args.serve_time_limit)
+    srv.close()
+    summ = serve.summarize(recs)
+    k = min(args.seq_sample, len(reqs))
+    seq = serve.summarize(serve.sequential_fp64(reqs[:k], systems[:k]))
+    srv2 = serve.Server(precision=hdmd.HDMD_MIXED, slots=args.slots, small_N=args.small_n,
+                        batch_pool_bytes=args.pool_gb << 30, budget=args.budget)
+    sub = serve.summarize(srv2.run(reqs[:k], systems[:k]))
+    srv2.close()
+    md_work = sum(r["N"] * r["nsteps"] for r in reqs if r["kind"] == 0)
+    line = {"metric": "serving: jobs/s and p50/p99 latency, Poisson 200 req/s of MD + FIRE",
+            "value": summ["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1000.0 * summ["makespan_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-pair/f64-accumulate", "data": "synthetic",
+            "config": {"workload": "serve_poisson200_md_fire_d3-8_N256-131072",
+                       "requests": len(reqs), "arrival_seconds": args.serve_seconds,
+                       "md_atom_steps": md_work, "budget_per_launch": args.budget,
+                       "slots": args.slots, "small_N": args.small_n},
+            "latency_p50_s": summ["p50_s"], "latency_p99_s": summ["p99_s"], "summary": summ,
+            "first_%d_requests" % k: {"server": sub, "sequential_fp64": seq}}
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -391,6 +433,20 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=16,
                     help="batched workload: jobs of the sequential FP64 comparison")
     ap.add_argument("--autotune", type=int, default=1, help="batched workload: run the autotuner")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="serving workload: seconds of Poisson arrivals")
+    ap.add_argument("--serve-time-limit", type=float, default=300.0,
+                    help="serving workload: stop serving after this many seconds")
+    ap.add_argument("--budget", type=int, default=256,
+                    help="serving workload: steps / FIRE iterations per job per launch")
+    ap.add_argument("--pool-gb", type=int, default=2,
+                    help="serving workload: batched-engine device pool (GiB)")
+    ap.add_argument("--slots", type=int, default=16,
+                    help="serving workload: concurrent system jobs")
+    ap.add_argument("--small-n", type=int, default=1024,
+                    help="serving workload: largest N served by the batched engine")
+    ap.add_argument("--seq-sample", type=int, default=24,
+                    help="serving workload: requests of the sequential FP64 comparison")
     ap.add_argument("--max-iter", type=int, default=20000,
                     help="batched workload: FIRE iteration limit per job")
     ap.add_argument("--eager", action="store_true",
@@ -402,6 +458,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

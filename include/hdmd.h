@@ -102,6 +102,13 @@ typedef struct {
     int64_t device_bytes;      /* device memory held by the system */
 } hdmd_info;
 
+/* Device bytes that create_system would allocate for these arguments (the
+ * lists at their initial capacity; they grow on overflow).  Same argument
+ * checks as create_system; no device work.  Lets a scheduler admit a job by
+ * free device memory before it creates the system.  *bytes receives it. */
+hdmd_status system_footprint(int d, int64_t N, double L, const double *diameters,
+                             const hdmd_potential *pot, hdmd_precision prec, int64_t *bytes);
+
 /* Create a system: d in 2..10 (else HDMD_E_UNSUPPORTED_D), N >= 2 atoms,
  * box side L, diameters[N] (host, > 0 and finite, copied).  Requires
  * L > 2 max sigma, so that only one periodic image of a pair can interact.

@@ -59,7 +59,7 @@ __device__ bool blk_build(const Dev &dv) {
     __syncthreads();
     for (int i = tid; i < dv.N; i += BT) scatter_one(dv, i);
     __syncthreads();
-    for (int c = tid; c < dv.ncells; c += BT) sort_cell(dv, c);
+    for (int p = tid; p < dv.N; p += BT) rank_one(dv, p);
     __syncthreads();
     for (int s = tid; s < dv.N; s += BT) reorder_one<D>(dv, s, 0);
     if (tid == 0) {

@@ -89,25 +89,28 @@ __device__ __forceinline__ void scan_cells(const Dev &dv) {
     }
 }
 
+// members of each subcell, in arrival order, into the scratch array cellid
+// (which the reorder step overwrites with the subcells of the new slots)
 __device__ __forceinline__ void scatter_one(const Dev &dv, int i) {
     int c = dv.cell_of[i];
     int slot = atomicAdd(&dv.cell_fill[c], 1);
-    dv.perm[dv.cell_start[c] + slot] = i;
+    dv.cellid[dv.cell_start[c] + slot] = i;
 }
 
-// members of subcell c ordered by caller id (insertion sort; cells are small)
-__device__ __forceinline__ void sort_cell(const Dev &dv, int c) {
-    int a = dv.cell_start[c], b = dv.cell_start[c + 1];
-    for (int p = a + 1; p < b; ++p) {
-        int v = dv.perm[p];
-        int key = dv.tid[v];
-        int q = p - 1;
-        while (q >= a && dv.tid[dv.perm[q]] > key) {
-            dv.perm[q + 1] = dv.perm[q];
-            --q;
-        }
-        dv.perm[q + 1] = v;
-    }
+// position p of the scattered members: the member's rank by caller id among
+// the members of its subcell places it, so every subcell comes out ordered by
+// caller id whatever order the atomics gave.  One thread per member; the
+// members of a subcell read the same entries in step, so a large subcell
+// (a single subcell holds every atom) costs its size squared over its size
+// threads rather than a serial sort.
+__device__ __forceinline__ void rank_one(const Dev &dv, int p) {
+    const int o = dv.cellid[p];
+    const int c = dv.cell_of[o];
+    const int a = dv.cell_start[c], b = dv.cell_start[c + 1];
+    const int key = dv.tid[o];
+    int r = 0;
+    for (int q = a; q < b; ++q) r += dv.tid[dv.cellid[q]] < key;
+    dv.perm[a + r] = o;
 }
 
 // new slot s: gather the state into cell order and write the build-time rows

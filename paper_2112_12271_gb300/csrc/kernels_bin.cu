@@ -86,11 +86,11 @@ __global__ void k_scatter(Dev dv, bool guarded) {
     if (i < dv.N) scatter_one(dv, i);
 }
 
-// step 4: sort each cell's members by caller id
+// step 4: place each cell's members in caller-id order
 __global__ void k_cell_sort(Dev dv, bool guarded) {
     if (skip(dv, guarded)) return;
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < dv.ncells) sort_cell(dv, c);
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < dv.N) rank_one(dv, p);
 }
 
 // step 5: gather the state into cell order; build-time rows
@@ -142,7 +142,7 @@ template <int D> void rebuild_impl(const Dev &dv, int buf, bool guarded, cudaStr
     k_assign<D><<<nblk(dv.N), NT, 0, s>>>(dv, guarded);
     k_scan<<<1, 1024, 0, s>>>(dv, guarded);
     k_scatter<<<nblk(dv.N), NT, 0, s>>>(dv, guarded);
-    k_cell_sort<<<nblk(dv.ncells), NT, 0, s>>>(dv, guarded);
+    k_cell_sort<<<nblk(dv.N), NT, 0, s>>>(dv, guarded);
     k_reorder<D><<<nblk(dv.N), NT, 0, s>>>(dv, buf, guarded);
 }
 template <int D> void trigger_impl(const Dev &dv, cudaStream_t s) {

@@ -15,8 +15,10 @@
 #include <algorithm>
 #include <cstddef>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hdmd.h"
@@ -32,6 +34,70 @@ struct GraphEx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
+
+// Device memory of every system comes from one stream-ordered pool per
+// device (cudaMallocFromPoolAsync / cudaFreeAsync on the system's stream).
+// cudaFree and cudaFreeHost wait for the whole device, so with them one
+// system's teardown would stall every system running on other streams;
+// the pool keeps up to 4 GiB of freed memory for the next system.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t device_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps pp = {};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        if (cudaMemPoolCreate(&mp, &pp) != cudaSuccess) return nullptr;
+        uint64_t keep = 4ull << 30;
+        cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = mp;
+    }
+    return g_pools[dev];
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t mp = device_pool();
+    if (!mp) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes, mp, s);
+}
+
+void pool_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// Pinned host words for the flag and reduction read-backs: 1 KiB slots cut
+// from 256 KiB pinned chunks that are kept for the life of the process, so
+// that no system ever calls cudaFreeHost.
+constexpr size_t kPinnedSlot = 1024;
+std::mutex g_pinned_mu;
+std::vector<char *> g_pinned_free;
+
+void *pinned_get() {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (g_pinned_free.empty()) {
+        char *chunk = nullptr;
+        if (cudaMallocHost((void **)&chunk, 256 * kPinnedSlot) != cudaSuccess) return nullptr;
+        for (int k = 255; k >= 0; --k) g_pinned_free.push_back(chunk + k * kPinnedSlot);
+    }
+    char *p = g_pinned_free.back();
+    g_pinned_free.pop_back();
+    return p;
+}
+
+void pinned_put(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_free.push_back((char *)p);
+}
+
+static_assert(sizeof(Flags) <= kPinnedSlot, "flag words exceed a pinned slot");
+static_assert(sizeof(double) * kNRed <= kPinnedSlot, "reduction words exceed a pinned slot");
 
 }  // namespace
 
@@ -109,10 +175,10 @@ template <class T>
 hdmd_status dalloc(hdmd_system *sys, T **p, size_t count) {
     size_t b = sizeof(T) * (count ? count : 1);
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, b);
+    cudaError_t e = pool_alloc(&q, b, sys->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(sys, HDMD_E_NOMEM, std::string("cudaMalloc of ") + std::to_string(b) +
+        return fail(sys, HDMD_E_NOMEM, std::string("device allocation of ") + std::to_string(b) +
                                            " bytes failed: " + cudaGetErrorString(e));
     }
     sys->allocs.push_back(q);
@@ -148,30 +214,33 @@ int default_lanes(int64_t N) {
 
 // expected longest list: atoms within max sigma + skin at the mean density,
 // with head-room; the build reports the true maximum and the list grows.
-int initial_capacity(const hdmd_system *sys) {
-    const int d = sys->d;
-    const double rho = (double)sys->N / std::pow(sys->L, d);
-    const double R = sys->sigma_max + sys->pot.skin;
+int initial_capacity(int d, int64_t N, double L, double sigma_max, double skin) {
+    const double rho = (double)N / std::pow(L, d);
+    const double R = sigma_max + skin;
     const double vball = std::pow(M_PI, 0.5 * d) * std::pow(R, d) / std::tgamma(1.0 + 0.5 * d);
     double est = 1.6 * rho * vball + 16.0;
-    est = std::min(est, (double)sys->N + 8.0);
+    est = std::min(est, (double)N + 8.0);
     return (int)est;
+}
+
+int initial_capacity(const hdmd_system *sys) {
+    return initial_capacity(sys->d, sys->N, sys->L, sys->sigma_max, sys->pot.skin);
 }
 
 hdmd_status alloc_lists(hdmd_system *sys, int cap) {
     const int G = sys->dv.G;
     cap = ((cap + G - 1) / G) * G;
     if (cap < G) cap = G;
-    if (sys->nbr) { cudaFree(sys->nbr); sys->nbr = nullptr; }
-    if (sys->code) { cudaFree(sys->code); sys->code = nullptr; }
+    if (sys->nbr) { pool_free(sys->nbr, sys->stream); sys->nbr = nullptr; }
+    if (sys->code) { pool_free(sys->code, sys->stream); sys->code = nullptr; }
     sys->bytes -= sys->list_bytes;
     const size_t cnt = (size_t)cap * sys->dv.Npad;
     void *a = nullptr, *b = nullptr;
-    cudaError_t e1 = cudaMalloc(&a, cnt * sizeof(int32_t));
-    cudaError_t e2 = e1 == cudaSuccess ? cudaMalloc(&b, cnt * sizeof(uint32_t)) : e1;
+    cudaError_t e1 = pool_alloc(&a, cnt * sizeof(int32_t), sys->stream);
+    cudaError_t e2 = e1 == cudaSuccess ? pool_alloc(&b, cnt * sizeof(uint32_t), sys->stream) : e1;
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
-        if (a) cudaFree(a);
+        if (e1 == cudaSuccess) pool_free(a, sys->stream);
         sys->list_bytes = 0;
         return fail(sys, HDMD_E_NOMEM, "Verlet list allocation of " +
                                            std::to_string(2 * cnt * 4) + " bytes failed");
@@ -700,15 +769,22 @@ hdmd_status fire_once(hdmd_system *sys, const hdmd_fire_params &p, hdmd_fire_res
 hdmd_status swap_alloc(hdmd_system *sys, int npairs, int scap) {
     SwapDev &sw = sys->sw;
     if (npairs <= sys->sw_cap_pairs && scap <= sw.scap) return HDMD_OK;
-    auto rel = [](void *p) { if (p) cudaFree(p); };
+    cudaStream_t s = sys->stream;
+    auto rel = [s](void *p) { pool_free(p, s); };
+    auto get = [s](auto **p, size_t bytes) {
+        void *q = nullptr;
+        const bool ok = pool_alloc(&q, bytes, s) == cudaSuccess;
+        *p = ok ? reinterpret_cast<typename std::remove_reference<decltype(**p)>::type *>(q) : nullptr;
+        return ok;
+    };
     if (npairs > sys->sw_cap_pairs) {
         rel(sw.ids); rel(sw.u); rel(sw.pairs); rel(sw.state); rel(sw.scount);
         sw.ids = nullptr; sw.u = nullptr; sw.pairs = nullptr; sw.state = nullptr; sw.scount = nullptr;
-        if (cudaMalloc((void **)&sw.ids, sizeof(int32_t) * 2 * npairs) != cudaSuccess ||
-            cudaMalloc((void **)&sw.u, sizeof(double) * npairs) != cudaSuccess ||
-            cudaMalloc((void **)&sw.pairs, sizeof(int32_t) * 2 * npairs) != cudaSuccess ||
-            cudaMalloc((void **)&sw.state, npairs) != cudaSuccess ||
-            cudaMalloc((void **)&sw.scount, sizeof(int32_t) * 2 * npairs) != cudaSuccess) {
+        if (!get(&sw.ids, sizeof(int32_t) * 2 * npairs) ||
+            !get(&sw.u, sizeof(double) * npairs) ||
+            !get(&sw.pairs, sizeof(int32_t) * 2 * npairs) ||
+            !get(&sw.state, npairs) ||
+            !get(&sw.scount, sizeof(int32_t) * 2 * npairs)) {
             cudaGetLastError();
             sys->sw_cap_pairs = 0;
             return fail(sys, HDMD_E_NOMEM, "SWAP pair buffers");
@@ -719,10 +795,10 @@ hdmd_status swap_alloc(hdmd_system *sys, int npairs, int scap) {
         sw.scap = 0;
     }
     if (!sw.owner) {
-        if (cudaMalloc((void **)&sw.owner, sizeof(unsigned long long) * sys->dv.Npad) != cudaSuccess ||
-            cudaMalloc((void **)&sw.slot_of, sizeof(int32_t) * sys->dv.Npad) != cudaSuccess ||
-            cudaMalloc((void **)&sw.overflow, sizeof(int) * 4) != cudaSuccess ||
-            cudaMalloc((void **)&sw.nacc, sizeof(unsigned long long)) != cudaSuccess) {
+        if (!get(&sw.owner, sizeof(unsigned long long) * sys->dv.Npad) ||
+            !get(&sw.slot_of, sizeof(int32_t) * sys->dv.Npad) ||
+            !get(&sw.overflow, sizeof(int) * 4) ||
+            !get(&sw.nacc, sizeof(unsigned long long))) {
             cudaGetLastError();
             return fail(sys, HDMD_E_NOMEM, "SWAP owner buffers");
         }
@@ -732,7 +808,7 @@ hdmd_status swap_alloc(hdmd_system *sys, int npairs, int scap) {
     if (scap > sw.scap || !sw.slist) {
         rel(sw.slist);
         sw.slist = nullptr;
-        if (cudaMalloc((void **)&sw.slist, sizeof(int32_t) * (size_t)2 * sys->sw_cap_pairs * scap) != cudaSuccess) {
+        if (!get(&sw.slist, sizeof(int32_t) * (size_t)2 * sys->sw_cap_pairs * scap)) {
             cudaGetLastError();
             sw.scap = 0;
             return fail(sys, HDMD_E_NOMEM, "SWAP neighbour lists");
@@ -747,7 +823,7 @@ void swap_free(hdmd_system *sys) {
     for (void *p : {(void *)sw.ids, (void *)sw.u, (void *)sw.pairs, (void *)sw.state, (void *)sw.owner,
                     (void *)sw.slot_of, (void *)sw.slist, (void *)sw.scount, (void *)sw.overflow,
                     (void *)sw.nacc})
-        if (p) cudaFree(p);
+        pool_free(p, sys->stream);
     sw = SwapDev{};
 }
 
@@ -799,17 +875,11 @@ hdmd_status validate_sys(hdmd_system *sys) {
     return HDMD_OK;
 }
 
-}  // namespace
-
-// =================================================================== C ABI
-extern "C" {
-
-hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
-                          const hdmd_potential *pot, hdmd_precision prec, void *cuda_stream,
-                          hdmd_system **out) {
-    hdmd_system *sys = nullptr;
-    if (!out) return fail(nullptr, HDMD_E_INVALID, "out is NULL");
-    *out = nullptr;
+// Argument checks of create_system; on success the largest diameter and the
+// subcells per axis.
+hdmd_status check_create_args(int d, int64_t N, double L, const double *diameters,
+                              const hdmd_potential *pot, hdmd_precision prec, double *smax_out,
+                              int *n_out) {
     if (d < 2 || d > kMaxD) return fail(nullptr, HDMD_E_UNSUPPORTED_D, "d must be in 2..10");
     if (N < 2 || N > (int64_t)1 << 28) return fail(nullptr, HDMD_E_INVALID, "N must be in 2..2^28");
     if (!(L > 0.0) || !std::isfinite(L)) return fail(nullptr, HDMD_E_INVALID, "L must be positive and finite");
@@ -835,6 +905,76 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     while (n > 2 && std::pow((double)n, d) > cap_cells) --n;
     if (std::pow((double)n, d) > 2.0e9) return fail(nullptr, HDMD_E_INVALID, "too many subcells");
 
+    *smax_out = smax;
+    *n_out = n;
+    return HDMD_OK;
+}
+
+// Bytes of the arrays create_system allocates, in its order and with the
+// same rounding as dalloc, plus the two list arrays at capacity cap.
+int64_t create_bytes(int d, int64_t N, int64_t ncells, int cap, int G) {
+    const size_t Np = (size_t)((N + 63) / 64 * 64), nd = (size_t)d * Np;
+    const size_t RF = kRowFloats(d), RD = kRowDoubles(d);
+    const size_t maxblocks = (Np * kMaxLanes + kStepNT - 1) / kStepNT;
+    const size_t nc = (size_t)ncells;
+    const Dev *dv = nullptr;
+    const hdmd_system *sy = nullptr;
+    int64_t b = 0;
+#define FB(expr, count) b += (int64_t)(sizeof(*(expr)) * ((size_t)(count) ? (size_t)(count) : 1))
+    FB(dv->x0, nd); FB(dv->dlt, nd); FB(dv->v, nd); FB(dv->F, nd);
+    FB(dv->sigma, Np); FB(sy->inv_mass_store, Np); FB(sy->st_f, nd);
+    FB(dv->img, nd); FB(dv->id, Np);
+    FB(dv->gs0, Np * RF); FB(dv->gs[0], Np * RF); FB(dv->gs[1], Np * RF);
+    FB(dv->gd[0], Np * RD); FB(dv->gd[1], Np * RD);
+    FB(dv->cell_count, nc); FB(dv->cell_fill, nc); FB(dv->cell_start, nc + 1);
+    FB(dv->cell_of, Np); FB(dv->perm, Np); FB(dv->cellid, Np); FB(dv->batch_start, nc + 1);
+    FB(dv->tx, nd); FB(dv->tv, nd); FB(dv->tsig, Np); FB(dv->tim, Np);
+    FB(dv->timg, nd); FB(dv->tid, Np);
+    FB(dv->nnbr, Np);
+    FB(dv->partials, (size_t)kNRed * maxblocks);
+    FB(dv->red, kNRed);
+    FB(dv->flags, 1);
+    FB(sy->st_x, nd); FB(sy->st_v, nd); FB(sy->st_m, Np); FB(sy->st_sig, Np);
+    FB(sy->st_i, nd); FB(sy->st_cnt, Np); FB(sy->st_off, Np + 1);
+    FB(sy->snap_x0, nd); FB(sy->snap_dlt, nd); FB(sy->snap_v, nd); FB(sy->snap_sig, Np);
+    FB(sy->snap_im, Np); FB(sy->snap_img, nd); FB(sy->snap_id, Np);
+#undef FB
+    int64_t c = ((int64_t)(cap + G - 1) / G) * G;
+    if (c < G) c = G;
+    b += (int64_t)(sizeof(int32_t) + sizeof(uint32_t)) * c * (int64_t)Np;   // nbr, code
+    return b;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+hdmd_status system_footprint(int d, int64_t N, double L, const double *diameters,
+                             const hdmd_potential *pot, hdmd_precision prec, int64_t *bytes) {
+    if (!bytes) return fail(nullptr, HDMD_E_INVALID, "bytes is NULL");
+    double smax = 0.0;
+    int n = 1;
+    hdmd_status st = check_create_args(d, N, L, diameters, pot, prec, &smax, &n);
+    if (st) return st;
+    int64_t ncells = 1;
+    for (int k = 0; k < d; ++k) ncells *= n;
+    *bytes = create_bytes(d, N, ncells, initial_capacity(d, N, L, smax, pot->skin), default_lanes(N));
+    return HDMD_OK;
+}
+
+hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
+                          const hdmd_potential *pot, hdmd_precision prec, void *cuda_stream,
+                          hdmd_system **out) {
+    hdmd_system *sys = nullptr;
+    if (!out) return fail(nullptr, HDMD_E_INVALID, "out is NULL");
+    *out = nullptr;
+    double smax = 0.0;
+    int n = 1;
+    {
+        hdmd_status cst = check_create_args(d, N, L, diameters, pot, prec, &smax, &n);
+        if (cst) return cst;
+    }
     sys = new hdmd_system();
     sys->d = d;
     sys->N = N;
@@ -892,8 +1032,9 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     DA2(sys->snap_x0, nd); DA2(sys->snap_dlt, nd); DA2(sys->snap_v, nd); DA2(sys->snap_sig, Np);
     DA2(sys->snap_im, Np); DA2(sys->snap_img, nd); DA2(sys->snap_id, Np);
 #undef DA2
-    if (cudaMallocHost((void **)&sys->h_flags, sizeof(Flags)) != cudaSuccess ||
-        cudaMallocHost((void **)&sys->h_red, sizeof(double) * kNRed) != cudaSuccess) {
+    sys->h_flags = (Flags *)pinned_get();
+    sys->h_red = (double *)pinned_get();
+    if (!sys->h_flags || !sys->h_red) {
         cudaGetLastError();
         return bail(fail(sys, HDMD_E_NOMEM, "pinned host allocation failed"));
     }
@@ -1064,13 +1205,15 @@ hdmd_status get_neighbors(hdmd_system *sys, int32_t *counts, int32_t *idx, int64
     if (total) *total = off[N];
     if (!idx || off[N] == 0) return HDMD_OK;
     if (off[N] > sys->st_idx_cap) {
-        if (sys->st_idx) cudaFree(sys->st_idx);
+        pool_free(sys->st_idx, sys->stream);
         sys->st_idx = nullptr;
-        if (cudaMalloc((void **)&sys->st_idx, sizeof(int32_t) * off[N]) != cudaSuccess) {
+        void *q = nullptr;
+        if (pool_alloc(&q, sizeof(int32_t) * off[N], sys->stream) != cudaSuccess) {
             cudaGetLastError();
             sys->st_idx_cap = 0;
             return fail(sys, HDMD_E_NOMEM, "staging for get_neighbors failed");
         }
+        sys->st_idx = (int32_t *)q;
         sys->st_idx_cap = off[N];
     }
     CK(cudaMemcpyAsync(sys->st_off, off.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, sys->stream));
@@ -1306,12 +1449,12 @@ hdmd_status destroy_system(hdmd_system *sys) {
     if (sys->stream) cudaStreamSynchronize(sys->stream);
     free_graphs(sys);
     swap_free(sys);
-    for (void *p : sys->allocs) cudaFree(p);
-    if (sys->nbr) cudaFree(sys->nbr);
-    if (sys->code) cudaFree(sys->code);
-    if (sys->st_idx) cudaFree(sys->st_idx);
-    if (sys->h_flags) cudaFreeHost(sys->h_flags);
-    if (sys->h_red) cudaFreeHost(sys->h_red);
+    for (void *p : sys->allocs) pool_free(p, sys->stream);
+    pool_free(sys->nbr, sys->stream);
+    pool_free(sys->code, sys->stream);
+    pool_free(sys->st_idx, sys->stream);
+    pinned_put(sys->h_flags);
+    pinned_put(sys->h_red);
     if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);
     if (sys->cap_stream2) cudaStreamDestroy(sys->cap_stream2);
     if (sys->cap_stream3) cudaStreamDestroy(sys->cap_stream3);

@@ -94,6 +94,7 @@ def lib():
         vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
         sig = {
             "create_system": [i32, i64, dbl, vp, vp, i32, vp, C.POINTER(vp)],
+            "system_footprint": [i32, i64, dbl, vp, vp, i32, C.POINTER(i64)],
             "set_state": [vp, vp, vp, vp],
             "set_diameters": [vp, vp],
             "get_state": [vp, vp, vp, vp, vp, vp],
@@ -167,6 +168,17 @@ def create_system(d, N, L, diameters, eps=1.0, skin=0.3, precision=HDMD_MIXED, s
                              stream if stream is not None else default_stream(), C.byref(h))
     _check(st)
     return h
+
+
+def system_footprint(d, N, L, diameters, eps=1.0, skin=0.3, precision=HDMD_MIXED):
+    """Device bytes create_system would allocate (no device work)."""
+    diam = _f64(diameters)
+    if diam.shape != (N,):
+        raise ValueError("diameters must have shape (N,)")
+    pot = Potential(0, eps, skin)
+    b = C.c_int64(0)
+    _check(lib().system_footprint(d, N, L, _p(diam), C.byref(pot), int(precision), C.byref(b)))
+    return b.value
 
 
 def set_state(h, x, v=None, masses=None):

@@ -151,3 +151,40 @@ def lattice(d: int, n: int, spacing: float = 1.0):
     L = n * spacing
     x = (g + 0.5) * spacing - 0.5 * L
     return x.astype(np.float64), float(L)
+
+
+def min_valid_N(d, phi, hi=1.2, lo=0.8):
+    """Smallest N whose box (polydisperse U[lo, hi] at packing fraction phi)
+    is longer than twice the largest diameter."""
+    mean_v = float(np.mean(sphere_volume(d, np.linspace(lo, hi, 201))))
+    return int(math.ceil(phi * (2.0 * hi * 1.02) ** d / mean_v))
+
+
+def c4_requests(duration=2.0, rate=200.0, seed=0):
+    """Poisson stream of MD and FIRE requests: arrivals at `rate` per second
+    over `duration` seconds; 50 % MD (steps uniform in 1000..10000, T = 1e-3,
+    dt = 0.005), 50 % FIRE; N lognormal with median 4096 and log-sd 1, clipped
+    to [256, 131072] and raised where needed so that the box exceeds twice the
+    largest diameter; d uniform in 3..8; polydisperse U[0.8, 1.2] at
+    phi = min(1.5 d 2^-d, 0.7)."""
+    rng = np.random.default_rng(seed)
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        d = int(rng.integers(3, 9))
+        phi = jamming_estimate(d)
+        N = int(np.clip(round(math.exp(rng.normal(math.log(4096), 1.0))), 256, 131072))
+        N = max(N, min_valid_N(d, phi))
+        kind = int(rng.integers(0, 2))
+        steps = int(rng.integers(1000, 10001))
+        reqs.append(dict(t=t, d=d, N=N, phi=phi, kind=kind, nsteps=steps,
+                         seed=int(rng.integers(0, 2 ** 31))))
+    return reqs
+
+
+def c4_system(req):
+    T = 1e-3 if req["kind"] == 0 else 0.0
+    return make_system(req["d"], req["N"], phi=req["phi"], dist="poly", T=T, seed=req["seed"],
+                       name="request")

@@ -65,3 +65,13 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "hdmd_oracle" not in txt, f
+
+
+def test_footprint_needs_no_gpu(libpath):
+    from paper_2112_12271_gb300 import hdmd
+    import numpy as np
+    small = hdmd.system_footprint(6, 4096, 5.0, np.ones(4096))
+    big = hdmd.system_footprint(6, 32768, 10.0, np.ones(32768))
+    assert 0 < small < big
+    with pytest.raises(hdmd.HDMDError):
+        hdmd.system_footprint(3, 10, 2.0, np.ones(10))      # box too small
