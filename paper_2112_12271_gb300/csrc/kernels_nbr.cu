@@ -35,7 +35,10 @@ namespace {
 constexpr int NT = 128;   // threads per block: 4 warps, one home batch each
 
 template <int D, bool WRAP>
-__global__ void __launch_bounds__(NT, 4) k_nbr_build(Dev dv, bool guarded) {
+#ifndef HDMD_NBR_MIN_BLOCKS
+#define HDMD_NBR_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(NT, HDMD_NBR_MIN_BLOCKS) k_nbr_build(Dev dv, bool guarded) {
     if (guarded && *((volatile int *)&dv.flags->rebuild) == 0) return;
     const int w = (blockIdx.x * NT + threadIdx.x) >> 5;
     if (w >= dv.batch_start[dv.ncells]) return;   // warp-uniform
