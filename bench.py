@@ -39,7 +39,7 @@ UNIT = "atom-steps/s"
 WORKLOAD = "d6_N32768_polydisperse_harmonic_L6_NVE_dt0.005_skin0.3"
 # c1: the benchmark system; c1l: the same density with N = 2^21 (L = 12), whose
 # working set exceeds L2 (the HBM-bound case used for ncu captures)
-WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0, "serve": 0}
+WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0, "serve": 0, "sweep": 0}
 
 
 def dist_env():
@@ -373,6 +373,62 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     return 0
 
+# ------------------------------------------------------------- dimension sweep
+def run_sweep(args):
+    """Dimension sweep d = 4..8 at N = 65536: FIRE to max|F_i| < 1e-10 (mixed
+    precision with the FP64 polish, and the plain FP64 form beside it), then
+    100 SWAP sweeps (p = 0.1, T = 1e-3) of the minimised packing."""
+    import torch
+    from paper_2112_12271_gb300 import build as B
+    from paper_2112_12271_gb300 import hdmd
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        c = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        c.record(stream)
+        c.synchronize()
+        return a.elapsed_time(c) / 1000.0, out
+
+    rows, total = [], 0.0
+    for d in range(4, 9):
+        s = W.c2_sweep(d, seed=0, N=args.sweep_n)
+        row = {"d": d, "N": s.N, "L": s.L}
+        with hdmd.System(s.d, s.L, s.sigma, s.x, precision=hdmd.HDMD_MIXED,
+                         stream=stream.cuda_stream) as g:
+            row["n_cell"] = g.info()["n_cell"]
+            t_fire, r = timed(lambda: g.fire(max_iter=args.sweep_max_iter))
+            t_swap, (acc, _) = timed(lambda: g.swap(1e-3, p=0.1, nsweeps=args.swap_sweeps, seed=d))
+            row.update(fire_s=t_fire, fire_iterations=r["iterations"],
+                       polish_iterations=r["polish_iterations"], converged=bool(r["converged"]),
+                       fmax=r["fmax"], E_pair=r["E_pair"], swap_s=t_swap,
+                       swap_ms_per_sweep=1000.0 * t_swap / args.swap_sweeps,
+                       swap_accepted=acc, swap_candidates=args.swap_sweeps * int(round(0.1 * s.N)))
+        total += t_fire + t_swap
+        if not args.no_fp64:
+            with hdmd.System(s.d, s.L, s.sigma, s.x, precision=hdmd.HDMD_FP64,
+                             stream=stream.cuda_stream) as g:
+                t64, r64 = timed(lambda: g.fire(max_iter=args.sweep_max_iter))
+            row.update(fp64_fire_s=t64, fp64_fire_iterations=r64["iterations"],
+                       fp64_converged=bool(r64["converged"]))
+        rows.append(row)
+        print(json.dumps({"sweep_row": row}), file=sys.stderr, flush=True)
+    line = {"metric": "dimension sweep: FIRE to |F|max<1e-10 + %d SWAP sweeps, d 4-8" % args.swap_sweeps,
+            "value": total, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1000.0 * total, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-pair/f64-accumulate+f64-polish", "data": "synthetic",
+            "config": {"workload": "sweep_d4-8_N%d_poly_fire_swap" % args.sweep_n,
+                       "N": args.sweep_n, "swap_sweeps": args.swap_sweeps, "p": 0.1, "T": 1e-3,
+                       "max_iter": args.sweep_max_iter},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
 # --------------------------------------------------------------------- serving
 def run_serve(args):
     """Poisson stream (200 requests/s) of MD and FIRE requests through the
@@ -448,7 +504,11 @@ def main():
     ap.add_argument("--seq-sample", type=int, default=24,
                     help="serving workload: requests of the sequential FP64 comparison")
     ap.add_argument("--max-iter", type=int, default=20000,
-                    help="batched workload: FIRE iteration limit per job")
+                    help="batched and sweep workloads: FIRE iteration limit per job")
+    ap.add_argument("--sweep-n", type=int, default=65536, help="sweep workload: atoms per system")
+    ap.add_argument("--swap-sweeps", type=int, default=100, help="sweep workload: SWAP sweeps")
+    ap.add_argument("--sweep-max-iter", type=int, default=200000,
+                    help="sweep workload: FIRE iteration limit")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu)")
     args = ap.parse_args()
@@ -460,6 +520,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

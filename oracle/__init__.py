@@ -14,6 +14,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   sphere_volume, n_cell, cell_index ... closed forms, hand-built examples
   neighbors_brute / neighbors_cells .. each other, hypercubic-lattice counts
                                        (2d, 2d^2), symmetry, O(N^2) brute force
+  neighbors_of / force_on ............ rows of the all-pairs routines,
+                                       lattice counts, shares summing to E, W
   forces ............................. two-body closed form, central finite
                                        differences of E, Newton's third law,
                                        virial = -sum x.grad U
@@ -71,6 +73,11 @@ def _load():
             for fn in (lib.orc_neighbors_brute, lib.orc_neighbors_cells):
                 fn.restype = i64
                 fn.argtypes = [i32, i64, dbl, vp, vp, dbl, i32, vp, vp, i64]
+            lib.orc_neighbors_of.restype = i64
+            lib.orc_neighbors_of.argtypes = [i32, i64, dbl, vp, vp, dbl, i32, i64, vp, i64]
+            lib.orc_force_on.restype = None
+            lib.orc_force_on.argtypes = [i32, i64, dbl, vp, vp, dbl, i64, vp,
+                                         C.POINTER(dbl), C.POINTER(dbl)]
             lib.orc_harmonic.restype = dbl
             lib.orc_harmonic.argtypes = [dbl, dbl, dbl, C.POINTER(dbl)]
             lib.orc_forces.restype = None
@@ -149,6 +156,19 @@ def neighbors_cells(x, sigma, L, skin, global_cut=False):
     return _neighbors(_load().orc_neighbors_cells, x, sigma, L, skin, global_cut)
 
 
+def neighbors_of(x, sigma, L, skin, i, global_cut=False):
+    """The list of atom i alone (ascending), by the all-pairs definition."""
+    x = _f64(x)
+    N, d = x.shape
+    sigma = _f64(sigma)
+    lib = _load()
+    c = lib.orc_neighbors_of(d, N, L, _p(x), _p(sigma), skin, int(global_cut), int(i), None, 0)
+    idx = np.zeros(max(c, 1), dtype=np.int32)
+    c2 = lib.orc_neighbors_of(d, N, L, _p(x), _p(sigma), skin, int(global_cut), int(i), _p(idx), c)
+    assert c2 == c
+    return idx[:c]
+
+
 def lists_as_sets(counts, idx):
     out, off = [], 0
     for c in counts:
@@ -182,6 +202,18 @@ def forces(x, sigma, L, eps=1.0, lists=None):
     _load().orc_forces(d, N, L, _p(x), _p(sigma), eps, _p(cnt), _p(idx), _p(F),
                        C.byref(E), C.byref(W))
     return F, E.value, W.value
+
+
+def force_on(x, sigma, L, i, eps=1.0):
+    """(F_i[d], e_i, w_i): force on atom i over all other atoms and its half
+    shares of the pair energy and virial."""
+    x = _f64(x)
+    N, d = x.shape
+    sigma = _f64(sigma)
+    Fi = np.zeros(d)
+    e, w = C.c_double(), C.c_double()
+    _load().orc_force_on(d, N, L, _p(x), _p(sigma), eps, int(i), _p(Fi), C.byref(e), C.byref(w))
+    return Fi, e.value, w.value
 
 
 def kinetic(v, mass=None):

@@ -141,6 +141,30 @@ int64_t orc_neighbors_brute(int d, int64_t N, double L, const double *x,
     return tot;
 }
 
+/* The list of one atom i by the same plain definition: every j != i whose
+ * minimum-image distance is below the list radius, ascending.  For checking
+ * sampled atoms of systems too large for the all-pairs routine.  Returns the
+ * count (idx may be NULL to count only; -1 if the count exceeds cap). */
+int64_t orc_neighbors_of(int d, int64_t N, double L, const double *x,
+                         const double *sigma, double skin, int global_cut,
+                         int64_t i, int32_t *idx, int64_t cap)
+{
+    double smax = max_of(sigma, N);
+    int64_t c = 0;
+    for (int64_t j = 0; j < N; ++j) {
+        if (j == i) continue;
+        double rc = list_radius(sigma[i], sigma[j], skin, global_cut, smax);
+        if (dist2(d, L, x, i, j) < rc * rc) {
+            if (idx) {
+                if (c >= cap) return -1;
+                idx[c] = (int32_t)j;
+            }
+            ++c;
+        }
+    }
+    return c;
+}
+
 static int cmp_i32(const void *a, const void *b)
 {
     int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
@@ -308,6 +332,33 @@ void orc_forces(int d, int64_t N, double L, const double *x, const double *sigma
     }
     *E = e;
     *W = w;
+}
+
+/* Force on one atom i, F_i = sum_{j != i} f_ij over every other atom (the
+ * plain definition), and i's half share of the pair energy and virial, so
+ * that the shares of all atoms sum to E and W.  For sampled atoms of systems
+ * too large for the all-pairs routine. */
+void orc_force_on(int d, int64_t N, double L, const double *x, const double *sigma,
+                  double eps, int64_t i, double *Fi, double *ei, double *wi)
+{
+    double e = 0.0, w = 0.0;
+    for (int k = 0; k < d; ++k) Fi[k] = 0.0;
+    for (int64_t j = 0; j < N; ++j) {
+        if (j == i) continue;
+        double dx[ORC_MAXD], r2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            dx[k] = orc_min_image(x[i * d + k] - x[j * d + k], L);
+            r2 += dx[k] * dx[k];
+        }
+        double s = 0.5 * (sigma[i] + sigma[j]), fr;
+        double r = sqrt(r2);
+        double u = orc_harmonic(r, s, eps, &fr);
+        for (int k = 0; k < d; ++k) Fi[k] += fr * dx[k];
+        e += 0.5 * u;
+        w += 0.5 * fr * r2;
+    }
+    *ei = e;
+    *wi = w;
 }
 
 /* Kinetic energy K = (1/2) sum m v^2. */

@@ -97,6 +97,32 @@ def test_cells_equal_brute(orc, d, N, L):
             assert inside == (j in sets[i])
 
 
+@pytest.mark.parametrize("row", read_golden("lattice_neighbor_counts.txt")[:6])
+def test_single_atom_lists_on_lattices(orc, row):
+    d, n, rad, expect = int(row[0]), int(row[1]), float(row[2]), int(row[3])
+    x, L = W.lattice(d, n)
+    sigma = np.ones(len(x))
+    for i in (0, len(x) // 2, len(x) - 1):
+        assert len(orc.neighbors_of(x, sigma, L, rad - 1.0, i)) == expect
+
+
+@pytest.mark.parametrize("d,N,L", [(3, 300, 4.6), (6, 400, 4.1), (9, 150, 3.05)])
+def test_single_atom_lists_and_forces_are_rows_of_all_pairs(orc, d, N, L):
+    x, sigma = _random_system(d, N, L, seed=3 * d + N)
+    cb, ib = orc.neighbors_brute(x, sigma, L, 0.3)
+    off = np.concatenate([[0], np.cumsum(cb)])
+    F, E, Wv = orc.forces(x, sigma, L)
+    es = ws = 0.0
+    for i in range(N):
+        assert (orc.neighbors_of(x, sigma, L, 0.3, i) == ib[off[i]:off[i + 1]]).all()
+        Fi, ei, wi = orc.force_on(x, sigma, L, i)
+        assert np.abs(Fi - F[i]).max() <= 1e-13 * max(np.abs(F).max(), 1e-300)
+        es += ei
+        ws += wi
+    assert es == pytest.approx(E, rel=1e-12)
+    assert ws == pytest.approx(Wv, rel=1e-12)
+
+
 def test_cells_need_two_subcells(orc):
     x, sigma = _random_system(3, 50, 2.5, 0)
     with pytest.raises(ValueError):
