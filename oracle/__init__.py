@@ -18,7 +18,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                                        lattice counts, shares summing to E, W
   forces ............................. two-body closed form, central finite
                                        differences of E, Newton's third law,
-                                       virial = -sum x.grad U
+                                       virial = -sum x.grad U (both laws)
+  morse / law ........................ closed-form values of Eq. (1), the
+                                       volume-scaled prefactors on two bodies
+  sigma_eff .......................... Table III of the paper (4 digits)
   md_steps ........................... time reversibility, energy drift ~ dt^2,
                                        head-on two-body collision
   fire ............................... |F|max < 1e-10, E -> 0 below jamming,
@@ -78,6 +81,12 @@ def _load():
             lib.orc_force_on.restype = None
             lib.orc_force_on.argtypes = [i32, i64, dbl, vp, vp, dbl, i64, vp,
                                          C.POINTER(dbl), C.POINTER(dbl)]
+            lib.orc_morse.restype = dbl
+            lib.orc_morse.argtypes = [dbl, dbl, dbl, dbl, C.POINTER(dbl)]
+            lib.orc_set_law.restype = i32
+            lib.orc_set_law.argtypes = [i32, dbl, i32]
+            lib.orc_sigma_eff.restype = dbl
+            lib.orc_sigma_eff.argtypes = [dbl, dbl, i64]
             lib.orc_harmonic.restype = dbl
             lib.orc_harmonic.argtypes = [dbl, dbl, dbl, C.POINTER(dbl)]
             lib.orc_forces.restype = None
@@ -183,6 +192,38 @@ def harmonic(r: float, s: float, eps: float = 1.0):
     fr = C.c_double()
     u = _load().orc_harmonic(r, s, eps, C.byref(fr))
     return u, fr.value
+
+
+def morse(r: float, s: float, eps: float = 1.0, a: float = 30.0):
+    """(U, |f|/r) of the truncated and shifted Morse law, Eq. (1)."""
+    fr = C.c_double()
+    u = _load().orc_morse(r, s, eps, a, C.byref(fr))
+    return u, fr.value
+
+
+def sigma_eff(a: float, T: float, npts: int = 200000) -> float:
+    """Effective hard-sphere diameter of the Morse law, Eq. (12)."""
+    return _load().orc_sigma_eff(a, T, npts)
+
+
+class law:
+    """Context manager selecting the pair law of every oracle routine:
+    kind "harmonic" or "morse" (stiffness a), eps_scale for the volume-scaled
+    prefactors eps_i = eps sigma_i^d mixed as sqrt(eps_i eps_j).  The setting
+    is process-wide while the block runs; the harmonic law with one eps is
+    restored on exit."""
+
+    def __init__(self, kind="harmonic", a=30.0, eps_scale=False):
+        self.args = ({"harmonic": 0, "morse": 1}[kind], float(a), int(bool(eps_scale)))
+
+    def __enter__(self):
+        if _load().orc_set_law(*self.args) != 0:
+            raise ValueError("bad pair law")
+        return self
+
+    def __exit__(self, *exc):
+        _load().orc_set_law(0, 30.0, 0)
+        return False
 
 
 def forces(x, sigma, L, eps=1.0, lists=None):

@@ -17,7 +17,12 @@
  *     Eqs. (7)-(9)); each checks the other;
  *   - the harmonic soft-sphere pair law U = (eps/2)(1 - r/s_ij)^2 for
  *     r < s_ij with s_ij = (s_i + s_j)/2 (the Lorentz mixing rule of
- *     Sec. II.A; the paper says the radial law is a user choice);
+ *     Sec. II.A; the paper says the radial law is a user choice), or the
+ *     paper's own truncated and shifted Morse law (Eq. (1)) with the
+ *     volume-scaled prefactors eps_i = sigma_i^d mixed as sqrt(eps_i eps_j)
+ *     (Sec. II.A), selected for every routine by orc_set_law;
+ *   - the effective hard-sphere diameter of the Morse law (Eq. (12)) behind
+ *     the packing fractions of Table III;
  *   - kick-drift-kick velocity Verlet (Sec. II.B);
  *   - FIRE 2.0 with the semi-implicit Euler integrator (Sec. II.B; the
  *     paper names the method but prints neither steps nor constants, so the
@@ -280,6 +285,63 @@ double orc_harmonic(double r, double s, double eps, double *fr)
     return 0.5 * eps * g * g;
 }
 
+/* The truncated and shifted Morse law, Eq. (1):
+ *   U(r) = eps [exp(-2a(r - s)) - 2 exp(-a(r - s)) + 1]   for r <= s,
+ * and 0 for r >= s (the two agree at r = s, where U = 0).  Its force on i
+ * from j is -dU/dr = eps [2a exp(-2a(r - s)) - 2a exp(-a(r - s))] along
+ * (x_i - x_j)/r; *fr receives that magnitude divided by r. */
+double orc_morse(double r, double s, double eps, double a, double *fr)
+{
+    if (r >= s) { *fr = 0.0; return 0.0; }
+    double e2 = exp(-2.0 * a * (r - s));
+    double e1 = exp(-a * (r - s));
+    *fr = (r > 0.0) ? eps * (2.0 * a * e2 - 2.0 * a * e1) / r : 0.0;
+    return eps * (e2 - 2.0 * e1 + 1.0);
+}
+
+/* The pair law every routine below applies, set process-wide (default:
+ * harmonic, one eps for all pairs).  kind 0 = harmonic, 1 = Morse with
+ * stiffness a.  eps_scale = 1 gives atom i the prefactor
+ * eps_i = eps sigma_i^d (Sec. II.A: prefactors scale with particle volume)
+ * and a pair eps_ij = sqrt(eps_i eps_j) (the mixing rule of Sec. II.A);
+ * eps_scale = 0 gives every pair eps.  Returns 0, or -1 for a bad kind. */
+static int g_law_kind = 0;
+static double g_law_a = 30.0;
+static int g_law_eps_scale = 0;
+
+int orc_set_law(int kind, double a, int eps_scale)
+{
+    if (kind != 0 && kind != 1) return -1;
+    g_law_kind = kind;
+    g_law_a = a;
+    g_law_eps_scale = eps_scale ? 1 : 0;
+    return 0;
+}
+
+/* U and |f|/r of atoms with diameters si, sj at distance r under the law
+ * set above. */
+static double pair_law(int d, double r, double si, double sj, double eps, double *fr)
+{
+    double s = 0.5 * (si + sj);
+    double e = eps;
+    if (g_law_eps_scale) e = sqrt((eps * pow(si, d)) * (eps * pow(sj, d)));
+    if (g_law_kind == 1) return orc_morse(r, s, e, g_law_a, fr);
+    return orc_harmonic(r, s, e, fr);
+}
+
+/* Effective hard-sphere diameter of the Morse law, Eq. (12):
+ *   sigma_eff(a, T) = integral_0^1 [1 - exp(-U_a(r)/T)] dr
+ * for unit diameter and prefactor, by the midpoint rule on npts points. */
+double orc_sigma_eff(double a, double T, int64_t npts)
+{
+    double h = 1.0 / (double)npts, sum = 0.0, fr;
+    for (int64_t k = 0; k < npts; ++k) {
+        double r = (k + 0.5) * h;
+        sum += 1.0 - exp(-orc_morse(r, 1.0, 1.0, a, &fr) / T);
+    }
+    return sum * h;
+}
+
 /* Pair forces F[N*d], pair energy E = sum_{i<j} U_ij and virial
  * W = sum_{i<j} (x_i - x_j).f_ij.  With counts == NULL every pair i<j is
  * visited (brute force); otherwise counts/idx hold full Verlet lists (as
@@ -298,9 +360,9 @@ void orc_forces(int d, int64_t N, double L, const double *x, const double *sigma
                     dx[k] = orc_min_image(x[i * d + k] - x[j * d + k], L);
                     r2 += dx[k] * dx[k];
                 }
-                double s = 0.5 * (sigma[i] + sigma[j]), fr;
+                double fr;
                 double r = sqrt(r2);
-                double u = orc_harmonic(r, s, eps, &fr);
+                double u = pair_law(d, r, sigma[i], sigma[j], eps, &fr);
                 if (u == 0.0 && fr == 0.0) continue;
                 for (int k = 0; k < d; ++k) {
                     F[i * d + k] += fr * dx[k];
@@ -320,9 +382,9 @@ void orc_forces(int d, int64_t N, double L, const double *x, const double *sigma
                     dx[k] = orc_min_image(x[i * d + k] - x[j * d + k], L);
                     r2 += dx[k] * dx[k];
                 }
-                double s = 0.5 * (sigma[i] + sigma[j]), fr;
+                double fr;
                 double r = sqrt(r2);
-                double u = orc_harmonic(r, s, eps, &fr);
+                double u = pair_law(d, r, sigma[i], sigma[j], eps, &fr);
                 for (int k = 0; k < d; ++k) F[i * d + k] += fr * dx[k];
                 e += 0.5 * u;
                 w += 0.5 * fr * r2;
@@ -350,9 +412,9 @@ void orc_force_on(int d, int64_t N, double L, const double *x, const double *sig
             dx[k] = orc_min_image(x[i * d + k] - x[j * d + k], L);
             r2 += dx[k] * dx[k];
         }
-        double s = 0.5 * (sigma[i] + sigma[j]), fr;
+        double fr;
         double r = sqrt(r2);
-        double u = orc_harmonic(r, s, eps, &fr);
+        double u = pair_law(d, r, sigma[i], sigma[j], eps, &fr);
         for (int k = 0; k < d; ++k) Fi[k] += fr * dx[k];
         e += 0.5 * u;
         w += 0.5 * fr * r2;
@@ -606,7 +668,7 @@ static double energy_with(int d, int64_t N, double L, const double *x,
     for (int64_t k = 0; k < N; ++k) {
         if (k == a || k == b) continue;
         double r = sqrt(dist2(d, L, x, a, k));
-        e += orc_harmonic(r, 0.5 * (sa + sigma[k]), eps, &fr);
+        e += pair_law(d, r, sa, sigma[k], eps, &fr);
     }
     return e;
 }

@@ -84,6 +84,42 @@ def polydisperse(rng, N: int, lo: float = 0.8, hi: float = 1.2) -> np.ndarray:
     return rng.uniform(lo, hi, size=N)
 
 
+def power_law_diameters(rng, N: int, d: int, R: float) -> np.ndarray:
+    """Diameters from Eq. (3): P(sigma) proportional to sigma^-d on
+    [R^(-1/2d), R^(1/2d)] (R = ratio of largest to smallest particle volume),
+    by inverting its cumulative distribution."""
+    lo, hi = R ** (-0.5 / d), R ** (0.5 / d)
+    a, b = lo ** (1 - d), hi ** (1 - d)
+    u = rng.random(N)
+    return (a - u * (a - b)) ** (1.0 / (1 - d))
+
+
+# Table III: packing fractions phi*_d of the paper's d = 3..6 benchmark runs
+# (the hard-sphere dynamical glass transition mapped to the Morse law with
+# a = 30 at T = 0.25).
+PHI_STAR = {3: 0.5980, 4: 0.4232, 5: 0.2847, 6: 0.1850}
+MORSE_A = 30.0      # Morse stiffness of the benchmark runs (Sec. II.A)
+PAPER_DT = 0.0016   # time step 6/(125 a) (Sec. II.A)
+PAPER_T = 0.25      # temperature of the benchmark runs (Sec. III)
+
+
+def paper_model(d, N, phi=None, T=PAPER_T, seed=0, R=None):
+    """The paper's own model (Sec. II.A): diameters from Eq. (3) with R = d,
+    masses m_i = sigma_i^d (prefactors eps_i = sigma_i^d are the pair law's
+    business), phi = phi*_d of Table III unless given, uniform positions,
+    Gaussian velocities at T for those masses.  The random positions overlap
+    badly: the paper removes that with a partial FIRE pushoff before MD."""
+    rng = np.random.default_rng(seed)
+    sigma = power_law_diameters(rng, N, d, float(d if R is None else R))
+    phi = PHI_STAR[d] if phi is None else phi
+    L = box_side(d, sigma, phi)
+    x = uniform_positions(rng, N, d, L)
+    mass = sigma ** d
+    v = thermal_velocities(rng, N, d, T, mass)
+    return System(d=d, L=float(L), sigma=sigma, x=x, v=v, mass=mass,
+                  name="paper_model_d%d_N%d" % (d, N), meta=dict(phi=phi, T=T, seed=seed))
+
+
 def make_system(d, N, *, phi=None, L=None, dist="poly", T=1e-3, seed=0, name=""):
     """One system: diameters, box, uniform positions, thermal velocities."""
     rng = np.random.default_rng(seed)

@@ -393,3 +393,85 @@ def test_swap_draw_properties(orc):
     assert hist.min() > 10
     p2, u2 = orc.swap_draw(12345, 4, 20000, 1000)
     assert not (p2 == pairs).all()
+
+
+# ------------------------------------------------------------------ Morse law (Eq. (1))
+@pytest.mark.parametrize("row", read_golden("table3_phi_star.txt"))
+def test_table3_effective_diameters(orc, row):
+    """Eq. (12) with the Morse law of Eq. (1) reproduces Table III: the
+    printed [sigma_eff(30, 0.25)]^d to 4 digits, and phi*_d = phi_d /
+    sigma_eff^d to within 1e-4 (the printed d = 3 entry, 0.5980, exceeds the
+    quotient 0.59794 by 0.6e-4)."""
+    d, phi_d, seff_d, phi_star = int(row[0]), float(row[1]), float(row[2]), float(row[3])
+    se = orc.sigma_eff(30.0, 0.25) ** d
+    assert round(se, 4) == seff_d
+    assert abs(phi_d / se - phi_star) <= 1e-4
+    assert W.PHI_STAR[d] == phi_star
+
+
+def test_morse_closed_forms(orc):
+    a, s, eps = 30.0, 1.1, 0.7
+    assert orc.morse(s, s, eps, a) == (0.0, 0.0)                    # truncated at r = s
+    assert orc.morse(s + 0.1, s, eps, a) == (0.0, 0.0)
+    r = s - math.log(2.0) / a                                         # exp(-a(r-s)) = 2
+    u, fr = orc.morse(r, s, eps, a)
+    assert u == pytest.approx(eps, rel=1e-14)                         # eps (4 - 4 + 1)
+    assert fr * r == pytest.approx(4.0 * a * eps, rel=1e-14)          # eps (2a 4 - 2a 2)
+    # just inside the cutoff U ~ eps a^2 (s - r)^2, the harmonic-like limit
+    dr = 1e-5
+    u, fr = orc.morse(s - dr, s, eps, a)
+    assert u == pytest.approx(eps * a * a * dr * dr, rel=1e-3)
+    assert fr * (s - dr) == pytest.approx(2 * eps * a * a * dr, rel=1e-3)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_volume_scaled_prefactors_two_bodies(orc, d):
+    """eps_i = sigma_i^d mixed as sqrt(eps_i eps_j) (Sec. II.A): a pair's
+    energy is (sigma_i sigma_j)^(d/2) times the unit-prefactor law."""
+    L = 10.0
+    x = np.zeros((2, d))
+    x[1, 0] = 0.93
+    sigma = np.array([0.9, 1.1])
+    for kind, base in (("morse", lambda r, s: orc.morse(r, s, 1.0, 30.0)[0]),
+                       ("harmonic", lambda r, s: orc.harmonic(r, s, 1.0)[0])):
+        with orc.law(kind, 30.0, eps_scale=True):
+            _, E, _ = orc.forces(x, sigma, L)
+        assert E == pytest.approx((0.9 * 1.1) ** (0.5 * d) * base(0.93, 1.0), rel=1e-13)
+
+
+@pytest.mark.parametrize("d", [3, 4, 6])
+def test_morse_force_is_minus_gradient(orc, d):
+    rng = np.random.default_rng(40 + d)
+    s = W.paper_model(d, 40, phi=0.3 * W.PHI_STAR[d], seed=d)
+    x, sigma, L = s.x, s.sigma, s.L
+    with orc.law("morse", 30.0, eps_scale=True):
+        F, E, _ = orc.forces(x, sigma, L)
+        assert E > 0
+        h = 1e-7
+        for i in rng.choice(len(x), 6, replace=False):
+            for k in range(d):
+                xp = x.copy(); xp[i, k] += h
+                xm = x.copy(); xm[i, k] -= h
+                fd = -(orc.forces(xp, sigma, L)[1] - orc.forces(xm, sigma, L)[1]) / (2 * h)
+                assert fd == pytest.approx(F[i, k], rel=1e-5, abs=1e-6 * np.abs(F).max())
+
+
+@pytest.mark.parametrize("d,delta", [(3, 0.1056), (4, 0.0991), (5, 0.0910), (6, 0.0834)])
+def test_power_law_diameters_polydispersity(d, delta):
+    """Eq. (3) with R = d: the polydispersity index Delta from the
+    distribution's closed-form moments (the paper prints 0.107, 0.099, 0.091,
+    0.083), and the sampler's moments against them."""
+    lo, hi = d ** (-0.5 / d), d ** (0.5 / d)
+
+    def moment(k):   # integral of sigma^(k-d) over [lo, hi], normalised
+        def prim(p, a, b):
+            return math.log(b / a) if p == -1 else (b ** (p + 1) - a ** (p + 1)) / (p + 1)
+        return prim(k - d, lo, hi) / prim(-d, lo, hi)
+
+    m1, m2 = moment(1), moment(2)
+    D = math.sqrt(m2 - m1 * m1) / m1
+    assert round(D, 4) == delta
+    sig = W.power_law_diameters(np.random.default_rng(d), 400000, d, float(d))
+    assert sig.min() >= lo and sig.max() <= hi
+    assert sig.mean() == pytest.approx(m1, rel=2e-3)
+    assert (sig.std() / sig.mean()) == pytest.approx(D, rel=2e-2)
