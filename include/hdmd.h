@@ -48,16 +48,26 @@ typedef enum {
 
 typedef enum { HDMD_FP64 = 0, HDMD_MIXED = 1 } hdmd_precision;
 
-/* Pair law.  kind 0: harmonic soft spheres
- *   U(r) = (eps/2) (1 - r/sigma_ij)^2 for r < sigma_ij, 0 beyond,
- * with the Lorentz mixing rule sigma_ij = (sigma_i + sigma_j)/2 (Sec. II.A;
- * the paper states the radial law is a user choice, Eq. (1) being its own
- * example).  skin: the Verlet-list skin s of Sec. II.C (list radius
- * sigma_ij + s).  Other kinds are rejected with HDMD_E_INVALID. */
+/* Pair law, with the Lorentz mixing rule sigma_ij = (sigma_i + sigma_j)/2
+ * (Sec. II.A; the paper states the radial law is a user choice).
+ *   kind 0: harmonic soft spheres
+ *     U(r) = (eps_ij/2) (1 - r/sigma_ij)^2 for r < sigma_ij, 0 beyond;
+ *   kind 1: the paper's truncated and shifted Morse law, Eq. (1),
+ *     U(r) = eps_ij [exp(-2a(r - sigma_ij)) - 2 exp(-a(r - sigma_ij)) + 1]
+ *     for r < sigma_ij, 0 beyond (a > 0: stiffness; the paper uses 30).
+ * eps_scale 0: eps_ij = eps for every pair; 1: each atom has the prefactor
+ * eps_i = eps sigma_i^d (prefactors scale with particle volume, Sec. II.A)
+ * and eps_ij = sqrt(eps_i eps_j) (the mixing rule of Sec. II.A).
+ * skin: the Verlet-list skin s of Sec. II.C (list radius sigma_ij + s).
+ * Other kinds, a <= 0 for kind 1, or eps_scale outside {0, 1} are rejected
+ * with HDMD_E_INVALID.  The batched engine and the allocation-free force
+ * call use kind 0 with one eps. */
 typedef struct {
     int kind;
     double eps;
     double skin;
+    double a;
+    int eps_scale;
 } hdmd_potential;
 
 /* Thermodynamic summary (Sec. II.E): pair energy E = sum_{i<j} U_ij, virial
@@ -70,7 +80,9 @@ typedef struct {
 
 /* FIRE 2.0 settings (Sec. II.B; constants of the published FIRE 2.0).
  * f_tol: stop when max_i |F_i| < f_tol.  polish_tol: in HDMD_MIXED systems
- * the iteration runs with FP32 pair forces until max_i |F_i| < polish_tol,
+ * the iteration runs with FP32 pair forces until max_i |F_i| < polish_tol
+ * times the law's stiffness factor (1 harmonic, 2 (a max sigma)^2 Morse), or
+ * until n_neg_max P <= 0 steps in a row show that FP32 rounding stalls it,
  * then continues with FP64 pair forces (0 disables the switch). */
 typedef struct {
     double dt0, dt_max, dt_min, f_inc, f_dec, alpha0, f_alpha, f_tol, polish_tol;

@@ -93,7 +93,7 @@ __device__ void blk_force(BatchJob &J, const Dev &dv, int lgG, bool fire, double
 #pragma unroll
         for (int k = 0; k < D; ++k) f[k] = 0;
         FT e = 0, w = 0;
-        if (i < dv.N) pair_forces<D, FP64P, FT>(dv, i, g, lgG, 0, f, e, w);
+        if (i < dv.N) pair_forces<D, FP64P, FT, 0>(dv, i, g, lgG, 0, f, e, w);
         for (int o = G >> 1; o > 0; o >>= 1) {
 #pragma unroll
             for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
@@ -278,6 +278,8 @@ __device__ void run_job(BatchJob &J, long long budget) {
                     J.fire[FP_SWITCH] = 0.0;
                     J.fire[FS_STATUS] = FIRE_RUNNING;
                     J.fire[FS_PHASE_ITER] = 0.0;
+                    J.fire[FS_NNEG] = 0.0;
+                    J.fire[FS_NPOS] = 0.0;
                     J.phase64 = 1;
                 }
                 __syncthreads();

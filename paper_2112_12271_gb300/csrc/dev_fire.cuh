@@ -4,6 +4,8 @@
 // parameters (FireSlot indices), red the reduced sums (Red indices) of the
 // forces and velocities at the current positions.  Order of tests: converged
 // (max_i |F_i| < f_tol), precision switch, max_iter; then the P = F.v rules.
+// The precision switch (FP32 -> FP64 pair forces) happens below the switch
+// threshold, or when the FP32 phase stalls (n_neg_max P <= 0 steps in a row).
 // Writes and returns the new status.
 #pragma once
 #include "common.cuh"
@@ -36,7 +38,11 @@ __device__ __forceinline__ int fire_scalar_update(double *fs, const double *red)
         } else {
             fs[FS_NPOS] = 0.0;
             fs[FS_NNEG] += 1.0;
-            if (fs[FS_NNEG] > fs[FP_NNEGMAX]) status = FIRE_NEGFAIL;
+            // too many P <= 0 steps in a row: with FP32 pair forces (a
+            // switch threshold is set) that means their rounding floor has
+            // been reached, so the FP64 phase takes over; otherwise FIRE fails
+            if (fs[FS_NNEG] > fs[FP_NNEGMAX])
+                status = fs[FP_SWITCH] > 0.0 ? FIRE_SWITCH : FIRE_NEGFAIL;
             if (!(fs[FP_INITDELAY] != 0.0 && fs[FS_ITER] < fs[FP_NDELAY])) {
                 dt = fmax(dt * fs[FP_FDEC], fs[FP_DTMIN]);
                 alpha = fs[FP_ALPHA0];

@@ -1,7 +1,13 @@
 // dev_force.cuh -- the pair force / energy / virial loop over one atom's
 // Verlet list, shared by the grid kernels (kernels_force.cu) and the batched
-// kernel (kernels_batch.cu).  Harmonic spheres: U = (eps/2)(1 - r/s_ij)^2 for
-// r < s_ij; force on i = (eps/s_ij)(1 - r/s_ij)(x_i - x_j)/r.
+// kernel (kernels_batch.cu).  LAW 0, harmonic spheres: U = (e/2)(1 - r/s)^2
+// for r < s = s_ij, force on i = (e/s)(1 - r/s)(x_i - x_j)/r.  LAW 1, the
+// truncated and shifted Morse law of Eq. (1): U = e [exp(-2a(r-s)) -
+// 2 exp(-a(r-s)) + 1] = e m^2 with m = exp(-a(r-s)) - 1 (evaluated by expm1,
+// which keeps its digits near r = s), force on i = 2 a e (m + 1) m
+// (x_i - x_j)/r.  e = eps_ij: eps, or with volume-scaled prefactors
+// eps (sigma_i sigma_j)^(d/2) = sqrt(eps_i eps_j), eps_i = eps sigma_i^d
+// (Sec. II.A), from the radii sigma/2 held in the rows.
 // Lane g of the atom's group of G = 1 << lgG lanes walks entries g, g+G, ...
 // and accumulates its share into f, e (sum of U) and w (sum of r.f); the
 // caller combines the lanes.  FP64P selects FP64 pair arithmetic on the
@@ -16,7 +22,19 @@
 
 namespace hdmd {
 
-template <int D, bool FP64P, typename FT>
+// pair prefactor from the radii hi, hj: eps, or eps (4 hi hj)^(D/2)
+template <int D, typename T>
+__device__ __forceinline__ T eps_pair(T eps, T hi, T hj, int scale) {
+    if (!scale) return eps;
+    const T p = T(4) * hi * hj;
+    T q = T(1);
+#pragma unroll
+    for (int k = 0; k < D / 2; ++k) q *= p;
+    if (D & 1) q *= sqrt(p);
+    return eps * q;
+}
+
+template <int D, bool FP64P, typename FT, int LAW = 0>
 __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG, int in_buf,
                                             FT (&f)[D], FT &e, FT &w) {
     constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
@@ -45,11 +63,20 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
             const double s = hi + rj[D];
             if (r2 < s * s) {
                 const double r = sqrt(r2);
-                const double gg = 1.0 - r / s;
-                const double fr = r > 0.0 ? (dv.eps / s) * gg / r : 0.0;
+                const double ee = eps_pair<D, double>(dv.eps, hi, rj[D], dv.eps_scale);
+                double fr, u;
+                if constexpr (LAW == 0) {
+                    const double gg = 1.0 - r / s;
+                    fr = r > 0.0 ? (ee / s) * gg / r : 0.0;
+                    u = 0.5 * ee * gg * gg;
+                } else {
+                    const double m = expm1(-dv.morse_a * (r - s));
+                    fr = r > 0.0 ? 2.0 * dv.morse_a * ee * (m + 1.0) * m / r : 0.0;
+                    u = ee * m * m;
+                }
 #pragma unroll
                 for (int k = 0; k < D; ++k) f[k] += (FT)(fr * dx[k]);
-                e += (FT)(0.5 * dv.eps * gg * gg);
+                e += (FT)u;
                 w += (FT)(fr * r2);
             }
         }
@@ -61,6 +88,8 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
         const float hi = ri[D];
         const float Lsc = dv.Lsc_f;
         const float eps = (float)dv.eps;
+        const float ma = (float)dv.morse_a;
+        const int scale = dv.eps_scale;
         constexpr int U = HDMD_FORCE_UNROLL;   // list entries in flight per lane
         const int64_t lstride = (int64_t)Np << lgG;
         int64_t pos0 = ((int64_t)i << lgG) + g;
@@ -100,15 +129,25 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
                 }
                 const float s = hi + rj[u][D];
                 if (r2 < s * s && r2 > 0.f) {
-                    const float inv_s = __frcp_rn(s);
                     const float rinv = rsqrtf(r2);
                     const float r = r2 * rinv;
-                    const float gg = fmaf(-r, inv_s, 1.f);
-                    const float fr = eps * inv_s * gg * rinv;
+                    const float ee = eps_pair<D, float>(eps, hi, rj[u][D], scale);
+                    if constexpr (LAW == 0) {
+                        const float inv_s = __frcp_rn(s);
+                        const float gg = fmaf(-r, inv_s, 1.f);
+                        const float fr = ee * inv_s * gg * rinv;
 #pragma unroll
-                    for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
-                    e = (FT)fmaf(0.5f * eps * gg, gg, (float)e);
-                    w = (FT)fmaf(fr, r2, (float)w);
+                        for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+                        e = (FT)fmaf(0.5f * ee * gg, gg, (float)e);
+                        w = (FT)fmaf(fr, r2, (float)w);
+                    } else {
+                        const float m = expm1f(-ma * (r - s));
+                        const float fr = 2.f * ma * ee * (m + 1.f) * m * rinv;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+                        e = (FT)fmaf(ee * m, m, (float)e);
+                        w = (FT)fmaf(fr, r2, (float)w);
+                    }
                 }
             }
         }

@@ -109,7 +109,10 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
 #pragma unroll
         for (int k = 0; k < D; ++k) f[k] = 0;
         FT e = 0, w = 0;
-        if (valid) pair_forces<D, FP64P, FT>(dv, i, g, lgG, cfg.in_buf, f, e, w);
+        if (valid) {
+            if (dv.law == 1) pair_forces<D, FP64P, FT, 1>(dv, i, g, lgG, cfg.in_buf, f, e, w);
+            else pair_forces<D, FP64P, FT, 0>(dv, i, g, lgG, cfg.in_buf, f, e, w);
+        }
         for (int o = G >> 1; o > 0; o >>= 1) {
 #pragma unroll
             for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);

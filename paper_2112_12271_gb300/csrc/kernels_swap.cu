@@ -151,10 +151,28 @@ __global__ void k_swap_claim(SwapDev sw, unsigned round) {
     atomicMin(&sw.owner[sw.pairs[2 * p + 1]], v);
 }
 
-__device__ __forceinline__ double harmonic_u(double r, double s, double eps) {
+// pair energy of diameters si, sj at distance r under the system's law
+// (harmonic or the Morse law of Eq. (1); prefactor eps or, volume-scaled,
+// eps (si sj)^(D/2))
+template <int D>
+__device__ __forceinline__ double pair_u(const Dev &dv, double r, double si, double sj) {
+    const double s = 0.5 * (si + sj);
     if (r >= s) return 0.0;
+    double e = dv.eps;
+    if (dv.eps_scale) {
+        const double p = si * sj;
+        double q = 1.0;
+#pragma unroll
+        for (int k = 0; k < D / 2; ++k) q *= p;
+        if (D & 1) q *= sqrt(p);
+        e *= q;
+    }
+    if (dv.law == 1) {
+        const double m = expm1(-dv.morse_a * (r - s));
+        return e * m * m;
+    }
     const double g = 1.0 - r / s;
-    return 0.5 * eps * g * g;
+    return 0.5 * e * g * g;
 }
 
 // FP64 distance of atoms a and b at the current positions x0 + dlt
@@ -198,21 +216,21 @@ __global__ void k_swap_exec(Dev dv, SwapDev sw, unsigned round) {
         if (lane == 0) atomicAdd(sw.npend, 1);
         return;
     }
-    const double si = dv.sigma[i], sj = dv.sigma[j], eps = dv.eps;
+    const double si = dv.sigma[i], sj = dv.sigma[j];
     double eb = 0.0, ea = 0.0;
     for (int t = lane; t < ni; t += 32) {
         const int b = Si[t];
         if (b == j) continue;
         const double r = dist64<D>(dv, i, b), sb = dv.sigma[b];
-        eb += harmonic_u(r, 0.5 * (si + sb), eps);
-        ea += harmonic_u(r, 0.5 * (sj + sb), eps);
+        eb += pair_u<D>(dv, r, si, sb);
+        ea += pair_u<D>(dv, r, sj, sb);
     }
     for (int t = lane; t < nj; t += 32) {
         const int b = Sj[t];
         if (b == i) continue;
         const double r = dist64<D>(dv, j, b), sb = dv.sigma[b];
-        eb += harmonic_u(r, 0.5 * (sj + sb), eps);
-        ea += harmonic_u(r, 0.5 * (si + sb), eps);
+        eb += pair_u<D>(dv, r, sj, sb);
+        ea += pair_u<D>(dv, r, si, sb);
     }
     eb = warp_sum(eb);
     ea = warp_sum(ea);

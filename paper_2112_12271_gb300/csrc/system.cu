@@ -710,7 +710,14 @@ hdmd_status fire_once(hdmd_system *sys, const hdmd_fire_params &p, hdmd_fire_res
     fs[FP_ALPHA0] = p.alpha0;
     fs[FP_FALPHA] = p.f_alpha;
     fs[FP_FTOL] = p.f_tol;
-    fs[FP_SWITCH] = (mixed && p.polish_tol > p.f_tol) ? p.polish_tol : 0.0;
+    // FP32 pair forces resolve max|F| down to about (pair stiffness) x (FP32
+    // position resolution): the switch threshold scales with the law's
+    // stiffness at contact relative to the harmonic law's, 1 (harmonic) or
+    // 2 (a sigma_max)^2 (Morse, Eq. (1))
+    const double stiff = sys->dv.law == 1 ? 2.0 * (sys->dv.morse_a * sys->sigma_max) *
+                                                (sys->dv.morse_a * sys->sigma_max)
+                                          : 1.0;
+    fs[FP_SWITCH] = (mixed && p.polish_tol > p.f_tol) ? p.polish_tol * stiff : 0.0;
     fs[FP_NDELAY] = (double)p.n_delay;
     fs[FP_NNEGMAX] = (double)p.n_neg_max;
     fs[FP_MAXITER] = (double)p.max_iter;
@@ -731,6 +738,8 @@ hdmd_status fire_once(hdmd_system *sys, const hdmd_fire_params &p, hdmd_fire_res
         sys->h_flags->fire[FP_SWITCH] = 0.0;
         sys->h_flags->fire[FS_STATUS] = FIRE_RUNNING;
         sys->h_flags->fire[FS_PHASE_ITER] = 0.0;
+        sys->h_flags->fire[FS_NNEG] = 0.0;
+        sys->h_flags->fire[FS_NPOS] = 0.0;
         CK(cudaMemcpyAsync(dv.flags->fire, sys->h_flags->fire, sizeof(double) * FS_COUNT,
                            cudaMemcpyHostToDevice, sys->stream));
         sys->rows64_valid = false;
@@ -885,7 +894,12 @@ hdmd_status check_create_args(int d, int64_t N, double L, const double *diameter
     if (!(L > 0.0) || !std::isfinite(L)) return fail(nullptr, HDMD_E_INVALID, "L must be positive and finite");
     if (!diameters) return fail(nullptr, HDMD_E_INVALID, "diameters is NULL");
     if (!pot) return fail(nullptr, HDMD_E_INVALID, "potential is NULL");
-    if (pot->kind != 0) return fail(nullptr, HDMD_E_INVALID, "only the harmonic pair law (kind 0) is available");
+    if (pot->kind != 0 && pot->kind != 1)
+        return fail(nullptr, HDMD_E_INVALID, "pair law kind must be 0 (harmonic) or 1 (Morse)");
+    if (pot->kind == 1 && (!(pot->a > 0.0) || !std::isfinite(pot->a)))
+        return fail(nullptr, HDMD_E_INVALID, "the Morse stiffness a must be positive and finite");
+    if (pot->eps_scale != 0 && pot->eps_scale != 1)
+        return fail(nullptr, HDMD_E_INVALID, "eps_scale must be 0 or 1");
     if (!(pot->eps > 0.0) || !std::isfinite(pot->eps)) return fail(nullptr, HDMD_E_INVALID, "eps must be positive");
     if (!(pot->skin >= 0.0) || !std::isfinite(pot->skin)) return fail(nullptr, HDMD_E_INVALID, "skin must be >= 0");
     if (prec != HDMD_FP64 && prec != HDMD_MIXED) return fail(nullptr, HDMD_E_INVALID, "unknown precision");
@@ -994,6 +1008,9 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     dv.invL = 1.0 / L;
     dv.skin = pot->skin;
     dv.eps = pot->eps;
+    dv.law = pot->kind;
+    dv.eps_scale = pot->eps_scale;
+    dv.morse_a = pot->kind == 1 ? pot->a : 0.0;
     dv.n = n;
     dv.ncells = 1;
     for (int k = 0; k < d; ++k) dv.ncells *= n;

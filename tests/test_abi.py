@@ -42,7 +42,7 @@ def test_errors_without_gpu_are_reported_not_raised(libpath):
     from paper_2112_12271_gb300 import hdmd
     lib = hdmd.lib()
     h = ctypes.c_void_p()
-    pot = hdmd.Potential(0, 1.0, 0.3)
+    pot = hdmd.potential(1.0, 0.3)
     import numpy as np
     diam = np.ones(10)
     st = lib.create_system(11, 10, 5.0, diam.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
@@ -54,6 +54,9 @@ def test_errors_without_gpu_are_reported_not_raised(libpath):
     bad = diam.copy(); bad[3] = -1.0
     st = lib.create_system(3, 10, 9.0, bad.ctypes.data, ctypes.byref(pot), 0, None, ctypes.byref(h))
     assert st == 1
+    bad_law = hdmd.potential(1.0, 0.3, law="morse", a=-1.0)
+    st = lib.create_system(3, 10, 9.0, diam.ctypes.data, ctypes.byref(bad_law), 0, None, ctypes.byref(h))
+    assert st == 1 and b"Morse stiffness" in lib.hdmd_last_error(None)
     assert lib.destroy_system(None) == 0
 
 
