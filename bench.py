@@ -39,7 +39,7 @@ UNIT = "atom-steps/s"
 WORKLOAD = "d6_N32768_polydisperse_harmonic_L6_NVE_dt0.005_skin0.3"
 # c1: the benchmark system; c1l: the same density with N = 2^21 (L = 12), whose
 # working set exceeds L2 (the HBM-bound case used for ncu captures)
-WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0, "serve": 0, "sweep": 0}
+WORKLOADS = {"c1": 32768, "c1l": 2 ** 21, "batch": 0, "serve": 0, "sweep": 0, "paper": 0}
 
 
 def dist_env():
@@ -373,6 +373,68 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     return 0
 
+# -------------------------------------------------------- the paper's own model
+def run_paper(args):
+    """The paper's benchmark protocol (Sec. III) at d = 3..6: its Morse law
+    (a = 30) with volume-scaled prefactors and masses, diameters of Eq. (3)
+    with R = d, phi*_d of Table III, T = 0.25, dt = 0.0016, skin 0.25.  Each
+    system is pushed off (FIRE with the bounded harmonic law removes the
+    overlaps of the random positions, which reach 1e27 in Morse energy),
+    given velocities at T, then run for args.paper_tau time units of MD
+    (625 steps each) with one SWAP pass (p = 0.1) per time unit.  Reports
+    atom-steps/s per d and the device time per list entry and step."""
+    import torch
+    from paper_2112_12271_gb300 import build as B
+    from paper_2112_12271_gb300 import hdmd
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.current_stream()
+    steps_per_tau = int(round(1.0 / W.PAPER_DT))
+    rows, total_atom_steps, total_s = [], 0, 0.0
+    for d in range(3, 7):
+        s = W.paper_model(d, args.paper_n, seed=d)
+        with hdmd.System(d, s.L, s.sigma, s.x, precision=hdmd.HDMD_MIXED,
+                         stream=stream.cuda_stream) as g:
+            g.fire(max_iter=20000)
+            x0 = g.state(v=False, img=False)["x"]
+        with hdmd.System(d, s.L, s.sigma, x0, s.v, s.mass, skin=0.25, precision=hdmd.HDMD_MIXED,
+                         stream=stream.cuda_stream, law="morse", a=W.MORSE_A, eps_scale=True) as g:
+            g.md_steps(steps_per_tau, W.PAPER_DT)          # warm-up: graphs, first builds
+            a = torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            acc = reb = 0
+            for tau in range(args.paper_tau):
+                t = g.md_steps(steps_per_tau, W.PAPER_DT)
+                reb += t["rebuilds"]
+                acc += g.swap(W.PAPER_T, p=0.1, nsweeps=1, seed=1000 * d + tau)[0]
+            c.record(stream)
+            c.synchronize()
+            sec = a.elapsed_time(c) / 1000.0
+            info = g.info()
+        n_steps = steps_per_tau * args.paper_tau
+        z = info["total_list_entries"] / s.N
+        rows.append({"d": d, "N": s.N, "phi_star": W.PHI_STAR[d], "L": s.L, "n_cell": info["n_cell"],
+                     "seconds": sec, "atom_steps_per_s": s.N * n_steps / sec,
+                     "ns_per_list_entry_step": 1e9 * sec / (n_steps * s.N * z),
+                     "mean_list_length": z, "rebuilds": reb, "swap_accepted": acc,
+                     "T_end": t["T"], "E_pair_per_atom": t["E_pair"] / s.N})
+        total_atom_steps += s.N * n_steps
+        total_s += sec
+        print(json.dumps({"paper_row": rows[-1]}), file=sys.stderr, flush=True)
+    line = {"metric": "paper model: atom-steps/s, Morse a=30, phi*_d, T=0.25, d 3-6 (MD + SWAP per tau)",
+            "value": total_atom_steps / total_s, "unit": "atom-steps/s", "n_gpus": 1,
+            "steps": args.paper_tau, "warmup": 1, "ms_per_step": 1000.0 * total_s / (4 * args.paper_tau),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-pair/f64-accumulate", "data": "synthetic",
+            "config": {"workload": "paper_model_morse_d3-6_N%d" % args.paper_n, "N": args.paper_n,
+                       "tau": args.paper_tau, "steps_per_tau": steps_per_tau, "dt": W.PAPER_DT,
+                       "skin": 0.25, "T": W.PAPER_T, "swap_p": 0.1},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
 # ------------------------------------------------------------- dimension sweep
 def run_sweep(args):
     """Dimension sweep d = 4..8 at N = 65536: FIRE to max|F_i| < 1e-10 (mixed
@@ -506,6 +568,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=20000,
                     help="batched and sweep workloads: FIRE iteration limit per job")
     ap.add_argument("--sweep-n", type=int, default=65536, help="sweep workload: atoms per system")
+    ap.add_argument("--paper-n", type=int, default=100000, help="paper workload: atoms per system")
+    ap.add_argument("--paper-tau", type=int, default=10, help="paper workload: time units of MD")
     ap.add_argument("--swap-sweeps", type=int, default=100, help="sweep workload: SWAP sweeps")
     ap.add_argument("--sweep-max-iter", type=int, default=200000,
                     help="sweep workload: FIRE iteration limit")
@@ -522,6 +586,8 @@ def main():
         return run_serve(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run_gpu(args)
 
 

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import read_golden
 from paper_2112_12271_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -139,3 +140,22 @@ def test_fire_first_iterations_follow_oracle(H, law, masses):
         dx -= s.L * np.round(dx / s.L)
         assert np.abs(dx).max() < 1e-10, (it, np.abs(dx).max())
         assert r["E_pair"] == pytest.approx(ref["E"], rel=1e-10)
+
+
+@pytest.mark.parametrize("row", read_golden("paper_list_sizes.txt"))
+def test_list_sizes_match_the_paper(H, row):
+    """The paper prints the mean list size of its runs at phi*_d (Sec. III).
+    After the pushoff and ten time units of MD at T = 0.25, the liquid's
+    mean list length (list radius sigma_ij + 0.25) is within 2 % of it (the
+    uniform random start, before the liquid forms contacts, is ~15 % lower,
+    and after one time unit still ~4 %)."""
+    d, nvl = int(row[0]), float(row[1])
+    s = W.paper_model(d, 20000, seed=40 + d)
+    with H.System(d, s.L, s.sigma, s.x, precision=H.HDMD_MIXED) as g:
+        g.fire(max_iter=20000)
+        x0 = g.state(v=False, img=False)["x"]
+    with H.System(d, s.L, s.sigma, x0, s.v, s.mass, skin=SKIN, precision=H.HDMD_MIXED, **LAW) as g:
+        g.md_steps(10 * int(round(1.0 / W.PAPER_DT)), W.PAPER_DT)
+        g.build_neighbors(force=True)
+        z = g.info()["total_list_entries"] / s.N
+    assert z == pytest.approx(nvl, rel=0.02), z
