@@ -23,7 +23,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                                        volume-scaled prefactors on two bodies
   sigma_eff .......................... Table III of the paper (4 digits)
   md_steps ........................... time reversibility, energy drift ~ dt^2,
-                                       head-on two-body collision
+                                       head-on two-body collision; Berendsen:
+                                       ideal-gas relaxation in closed form
   fire ............................... |F|max < 1e-10, E -> 0 below jamming,
                                        two spheres relax to contact
   swap ............................... brute dE, equal diameters always
@@ -96,7 +97,7 @@ def _load():
             lib.orc_kinetic.argtypes = [i32, i64, vp, vp]
             lib.orc_md_steps.restype = i64
             lib.orc_md_steps.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl,
-                                         dbl, i64, vp, i32, vp]
+                                         dbl, i64, vp, i32, vp, dbl, dbl]
             lib.orc_fire.restype = i32
             lib.orc_fire.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl, vp,
                                      vp, vp]
@@ -265,8 +266,10 @@ def kinetic(v, mass=None):
 
 
 # --------------------------------------------------------------- integrators
-def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None, F=None):
-    """Velocity Verlet in place on copies; returns dict(x, v, img, F, E, W, K, builds)."""
+def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None, F=None,
+             T_target=0.0, tau=0.0):
+    """Velocity Verlet on copies (NVE, or NVT with the Berendsen factor
+    when tau > 0); returns dict(x, v, img, F, E, W, K, builds)."""
     x = _f64(x).copy()
     v = _f64(v).copy()
     N, d = x.shape
@@ -277,7 +280,8 @@ def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None,
     F = np.zeros_like(x) if F is None else _f64(F).copy()
     th = np.zeros(3)
     b = _load().orc_md_steps(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
-                             dt, int(nsteps), _p(F), int(have_F), _p(th))
+                             dt, int(nsteps), _p(F), int(have_F), _p(th), float(T_target),
+                             float(tau))
     return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b))
 
 

@@ -506,11 +506,16 @@ static double wrap(double x, double L, int32_t *img)
 /* velocity Verlet                                                      */
 /* ------------------------------------------------------------------ */
 
-/* nsteps of kick-drift-kick velocity Verlet in NVE (Sec. II.B: the
- * leapfrog "kick-drift-kick" variant; no thermostat here).  One step:
+/* nsteps of kick-drift-kick velocity Verlet (Sec. II.B: the leapfrog
+ * "kick-drift-kick" variant).  One step:
  *   v += (dt/2) F/m;  x += dt v, wrapped with image counts;
  *   rebuild the Verlet list if the trigger fires;  F = F(x);
- *   v += (dt/2) F/m.
+ *   v += (dt/2) F/m;
+ *   with tau > 0 (NVT): v *= lambda, the Berendsen factor (Berendsen et al.
+ *   1984, the thermostat of Sec. II.E, applied in the second kick as the
+ *   paper does) lambda = sqrt(1 + (dt/tau)(T_target/T - 1)), where T is the
+ *   kinetic temperature 2K/(d(N-1)) at the end of the previous step (at the
+ *   start of the call for the first step), and lambda = 1 when T = 0.
  * F must hold the forces at the incoming x (have_F != 0) or is computed
  * first from the list (have_F == 0); it holds those at the outgoing x on
  * return.  thermo[0..2] = E_pair, virial W, kinetic K at the end.
@@ -518,10 +523,11 @@ static double wrap(double x, double L, int32_t *img)
 int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *img,
                      const double *sigma, const double *mass, double eps,
                      double skin, double dt, int64_t nsteps, double *F, int have_F,
-                     double *thermo)
+                     double *thermo, double T_target, double tau)
 {
     orc_vl vl = {0};
     double E = 0.0, W = 0.0;
+    double T_prev = 2.0 * orc_kinetic(d, N, v, mass) / ((double)d * (double)(N - 1));
     vl_build(&vl, d, N, L, x, sigma, skin);
     if (!have_F) orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
     for (int64_t step = 0; step < nsteps; ++step) {
@@ -538,6 +544,12 @@ int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *
         for (int64_t i = 0; i < N; ++i) {
             double m = mass ? mass[i] : 1.0;
             for (int k = 0; k < d; ++k) v[i * d + k] += 0.5 * dt * F[i * d + k] / m;
+        }
+        if (tau > 0.0) {
+            double lambda = 1.0;
+            if (T_prev > 0.0) lambda = sqrt(fmax(0.0, 1.0 + (dt / tau) * (T_target / T_prev - 1.0)));
+            for (int64_t a = 0; a < N * d; ++a) v[a] *= lambda;
+            T_prev = 2.0 * orc_kinetic(d, N, v, mass) / ((double)d * (double)(N - 1));
         }
     }
     if (nsteps == 0) orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);

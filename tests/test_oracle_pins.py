@@ -475,3 +475,38 @@ def test_power_law_diameters_polydispersity(d, delta):
     assert sig.min() >= lo and sig.max() <= hi
     assert sig.mean() == pytest.approx(m1, rel=2e-3)
     assert (sig.std() / sig.mean()) == pytest.approx(D, rel=2e-2)
+
+
+# ------------------------------------------------------------------ Berendsen thermostat
+def _ideal_gas(d=3, N=400, seed=3):
+    """Atoms too small to touch (sigma = 1e-3 in a box of side 6): no forces.
+    Runs use a skin of 2 so that the box holds only 3 subcells per axis."""
+    rng = np.random.default_rng(seed)
+    L = 6.0
+    x = W.uniform_positions(rng, N, d, L)
+    sigma = np.full(N, 1e-3)
+    v = W.thermal_velocities(rng, N, d, 0.7)
+    return x, v, sigma, L
+
+
+def test_berendsen_ideal_gas_relaxes_exponentially(orc):
+    """Without forces T_{n+1} = lambda^2 T_n = T_n + (dt/tau)(T_t - T_n), so
+    T_n - T_t = (T_0 - T_t)(1 - dt/tau)^n (Berendsen et al. 1984)."""
+    x, v, sigma, L = _ideal_gas()
+    N, d = x.shape
+    T0 = 2 * orc.kinetic(v) / (d * (N - 1))
+    assert T0 == pytest.approx(0.7, rel=1e-12)
+    dt, tau, Tt = 0.005, 0.1, 0.25
+    for n in (1, 7, 40):
+        r = orc.md_steps(x, v, sigma, L, n, dt, skin=2.0, T_target=Tt, tau=tau)
+        T = 2 * r["K"] / (d * (N - 1))
+        assert T - Tt == pytest.approx((T0 - Tt) * (1 - dt / tau) ** n, rel=1e-10)
+
+
+def test_berendsen_with_tau_equal_dt_hits_the_target_in_one_step(orc):
+    x, v, sigma, L = _ideal_gas(d=4, N=300, seed=5)
+    N, d = x.shape
+    r = orc.md_steps(x, v, sigma, L, 1, 0.004, skin=2.0, T_target=0.3, tau=0.004)
+    assert 2 * r["K"] / (d * (N - 1)) == pytest.approx(0.3, rel=1e-12)
+    r0 = orc.md_steps(x, v, sigma, L, 1, 0.004, skin=2.0)       # NVE: unchanged
+    assert r0["K"] == pytest.approx(orc.kinetic(v), rel=1e-14)
