@@ -169,12 +169,22 @@ hdmd_status get_neighbors(hdmd_system *sys, int32_t *counts, int32_t *idx,
  * (get_state reads them). */
 hdmd_status compute_forces(hdmd_system *sys, double *energy, double *virial);
 
-/* nsteps of kick-drift-kick velocity Verlet in NVE (Sec. II.B) with time
- * step dt, the displacement trigger checked after every drift on the
- * device and the lists rebuilt there when it fires.  last (nullable)
- * receives the thermodynamic state after the final step.  On list overflow
- * the call restores its starting state, grows the lists and runs again. */
+/* nsteps of kick-drift-kick velocity Verlet (Sec. II.B) with time step dt,
+ * in NVE or, after set_thermostat, NVT; the displacement trigger is checked
+ * after every drift on the device and the lists rebuilt there when it
+ * fires.  last (nullable) receives the thermodynamic state after the final
+ * step.  On list overflow the call restores its starting state, grows the
+ * lists and runs again. */
 hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last);
+
+/* Berendsen thermostat (Berendsen et al. 1984; the NVT control of
+ * Sec. II.E, which the paper applies inside the second kick of each step,
+ * Sec. II.B).  With tau > 0 every later md_steps ends each step's second
+ * kick with v *= lambda, lambda = sqrt(1 + (dt/tau)(T_target/T - 1)), T the
+ * kinetic temperature 2K/(d(N-1)) at the end of the previous step (at the
+ * start of the call for its first step; lambda = 1 when T = 0).  tau <= 0
+ * returns to NVE.  T_target must be >= 0 and finite (HDMD_E_INVALID). */
+hdmd_status set_thermostat(hdmd_system *sys, double T_target, double tau);
 
 /* FIRE 2.0 minimisation (Sec. II.B).  params NULL takes the defaults
  * (dt0 0.005, dt_max 0.05, dt_min 1e-4, f_inc 1.1, f_dec 0.5, alpha0 0.25,

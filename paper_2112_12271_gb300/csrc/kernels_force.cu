@@ -4,8 +4,9 @@
 // of the list (Sec. II.C) and the FP64 reductions of the thermodynamic and
 // FIRE scalars (Sec. II.B FIRE, Sec. II.E getthermo).
 //
-// Pair law: harmonic soft spheres, U = (eps/2)(1 - r/s_ij)^2 for r < s_ij,
-// s_ij = (s_i + s_j)/2, force on i from j = (eps/s_ij)(1 - r/s_ij)(x_i-x_j)/r.
+// Pair law: harmonic soft spheres or the Morse law of Eq. (1), see
+// dev_force.cuh.  NVT: the Berendsen factor scales the second kick (the
+// paper fuses its thermostat into that kick, Sec. II.B).
 //
 // Thread mapping: G consecutive lanes share one atom (G in 1..32); lane g
 // walks list entries g, g+G, ... (coalesced thanks to the list layout), the
@@ -40,19 +41,38 @@ constexpr int NT = kStepNT;   // one wave of blocks at the benchmark size
 // unsigned integers, NaN above all) in a word of its own; the last block
 // (ticket, no waiting) takes the maximum over all blocks and turns it into
 // the rebuild flag and, inside a CUDA graph, into the IF condition.
+// With a thermostat (nvt != 0) the same ticket also folds sum m v^2 of the
+// thermostatted velocities (per-block partials at partials[maxblocks + b],
+// summed in a fixed order) into the Berendsen factor of the next step:
+// lambda = sqrt(1 + rate (T_target/T - 1)), T = sum m v^2 / (d (N - 1)).
+__device__ __forceinline__ double block_sum_fixed(double a, double *ws) {
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = a;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    return t;   // valid in thread 0
+}
+
 __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bool blk_bad,
-                                             unsigned long long cond) {
+                                             unsigned long long cond, int nvt = 0,
+                                             double kin = 0.0, double rate = 0.0,
+                                             double T_target = 0.0) {
     __shared__ bool last;
     __shared__ unsigned wmax[32];
+    __shared__ double wsum[32];
     unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(blk_max_d2));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
     if (blk_bad) atomicOr(&dv.flags->error, (int)ERR_LOST);
     __syncthreads();
+    const double kblk = nvt ? block_sum_fixed(kin, wsum) : 0.0;
     unsigned *part = reinterpret_cast<unsigned *>(dv.partials);   // one word per block
     if (threadIdx.x == 0) {
         unsigned b = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, wmax[w]);
         part[blockIdx.x] = b;
+        if (nvt) dv.partials[(size_t)dv.maxblocks + blockIdx.x] = kblk;
         __threadfence();
         const unsigned t = atomicAdd(&dv.flags->counter, 1u);
         last = (t == gridDim.x - 1);
@@ -65,6 +85,17 @@ __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bo
     b = __reduce_max_sync(0xffffffffu, b);
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = b;
     __syncthreads();
+    if (nvt) {
+        double k2 = 0.0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
+            k2 += __ldcg(dv.partials + (size_t)dv.maxblocks + k);
+        k2 = block_sum_fixed(k2, wsum);
+        if (threadIdx.x == 0) {
+            const double T = k2 / ((double)dv.d * (double)(dv.N - 1));
+            dv.flags->nvt_T = T;
+            dv.flags->nvt_lambda = T > 0.0 ? sqrt(fmax(0.0, 1.0 + rate * (T_target / T - 1.0))) : 1.0;
+        }
+    }
     if (threadIdx.x == 0) {
         unsigned m = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
@@ -136,6 +167,11 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
     const bool merged = cfg.kick2 && cfg.kick1_drift;
     const double kick = merged ? cfg.dt : cfg.halfdt;
     const bool do_kick = cfg.kick2 || cfg.kick1_drift;
+    // Berendsen NVT: the second kick ends in v *= lambda (the paper fuses the
+    // thermostat into it); sum m v^2 of those velocities feeds the next lambda
+    const bool nvt = cfg.nvt && cfg.kick2;
+    const double lam = nvt ? dv.flags->nvt_lambda : 1.0;
+    double kin = 0.0;
     for (int t = threadIdx.x; t < APB * D; t += NT) {
         const int k = t / APB, a = t - k * APB, ii = base + a;
         if (ii >= dv.N) continue;
@@ -145,7 +181,13 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
         const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
         const double Fm = dv.inv_mass ? F * im : F;
         double v = dv.v[o];
-        if (do_kick) v += kick * Fm;
+        if (nvt) {
+            const double vf = (v + cfg.halfdt * Fm) * lam;
+            kin += vf * vf / im;
+            v = cfg.kick1_drift ? vf + cfg.halfdt * Fm : vf;
+        } else if (do_kick) {
+            v += kick * Fm;
+        }
         if (cfg.thermo) acc[R_K2] += v * v / im;
         if (cfg.fire_red) {
             acc[R_P] += F * v;
@@ -195,7 +237,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
         }
         float m = 0.f;
         for (int a = threadIdx.x; a < APB; a += NT) m = fmaxf(m, sD2[a]);
-        trigger_fold(dv, m, false, cfg.cond_rebuild);
+        trigger_fold(dv, m, false, cfg.cond_rebuild, nvt ? 1 : 0, kin, cfg.nvt_rate, cfg.nvt_T);
     }
     if (cfg.thermo || cfg.fire_red) {
         const bool last = block_reduce_and_fold<NT>(dv, acc, R_BAD + 1, dv.maxblocks, sh);

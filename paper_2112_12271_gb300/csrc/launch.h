@@ -52,6 +52,9 @@ struct StepCfg {
     int fire_red;        // reduce P, v.v, v.F/m, F.F/m^2, F.F, max|F_i|^2 and run
                          // the FIRE scalar update in the last block
     double dt, halfdt;
+    int nvt;             // Berendsen NVT: second kick scaled by flags->nvt_lambda
+    double nvt_rate;     // dt / tau
+    double nvt_T;        // target temperature
     unsigned long long cond_rebuild;  // graph conditional set to the trigger (0: none)
     unsigned long long cond_loop;     // FIRE while-conditional (0: none)
 };

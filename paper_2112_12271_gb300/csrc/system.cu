@@ -120,6 +120,7 @@ struct hdmd_system {
     bool graphs_ok = true;
     std::string graph_err;
     double sigma_max = 0;
+    double nvt_T = 0.0, nvt_tau = 0.0;   // Berendsen thermostat (tau <= 0: NVE)
     bool unit_mass = true;
     double *inv_mass_store = nullptr;
     double *st_f = nullptr;
@@ -369,6 +370,11 @@ StepCfg base_cfg(const hdmd_system *sys, double dt) {
     c.dt = dt;
     c.halfdt = 0.5 * dt;
     c.fp64_pairs = sys->prec == HDMD_FP64 ? 1 : 0;
+    if (sys->nvt_tau > 0.0 && dt > 0.0) {
+        c.nvt = 1;
+        c.nvt_rate = dt / sys->nvt_tau;
+        c.nvt_T = sys->nvt_T;
+    }
     return c;
 }
 
@@ -512,6 +518,23 @@ hdmd_status snapshot(hdmd_system *sys, bool restore) {
     return HDMD_OK;
 }
 
+// Berendsen factor of the first step of an md_steps call, from the kinetic
+// temperature of the current velocities (a force pass with the thermo sums)
+hdmd_status nvt_prepare(hdmd_system *sys, int buf, bool fp64, double dt) {
+    hdmd_status st = force_only(sys, buf, fp64, true);
+    if (st) return st;
+    st = read_flags(sys);
+    if (st) return st;
+    const double T = sys->h_red[R_K2] / ((double)sys->d * (double)(sys->N - 1));
+    const double rate = dt / sys->nvt_tau;
+    sys->h_flags->nvt_lambda = T > 0.0 ? std::sqrt(std::max(0.0, 1.0 + rate * (sys->nvt_T / T - 1.0))) : 1.0;
+    sys->h_flags->nvt_T = T;
+    CK(cudaMemcpyAsync(&sys->dv.flags->nvt_lambda, &sys->h_flags->nvt_lambda, 2 * sizeof(double),
+                       cudaMemcpyHostToDevice, sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    return HDMD_OK;
+}
+
 constexpr int kChunk = 64;
 
 hdmd_status md_once(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
@@ -529,6 +552,10 @@ hdmd_status md_once(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *la
         st = force_only(sys, sys->buf, fp64, false);
         if (st) return st;
         sys->F_valid = true;
+    }
+    if (sys->nvt_tau > 0.0 && nsteps > 0) {
+        st = nvt_prepare(sys, sys->buf, fp64, dt);
+        if (st) return st;
     }
     int cur = sys->buf;
     if (nsteps > 0) {
@@ -1420,6 +1447,17 @@ hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_ou
     st = snapshot(sys, true);
     if (st) return st;
     return build_forced(sys, buf0);
+}
+
+hdmd_status set_thermostat(hdmd_system *sys, double T_target, double tau) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!(T_target >= 0.0) || !std::isfinite(T_target) || std::isnan(tau))
+        return fail(sys, HDMD_E_INVALID, "T_target must be >= 0 and finite");
+    sys->nvt_T = T_target;
+    sys->nvt_tau = tau > 0.0 && std::isfinite(tau) ? tau : 0.0;
+    free_graphs(sys);   // the step graphs hold the thermostat constants
+    return HDMD_OK;
 }
 
 hdmd_status get_info(hdmd_system *sys, hdmd_info *info) {

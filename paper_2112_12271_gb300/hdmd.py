@@ -112,6 +112,7 @@ def lib():
             "get_neighbors": [vp, vp, vp, C.POINTER(i64)],
             "compute_forces": [vp, C.POINTER(dbl), C.POINTER(dbl)],
             "md_steps": [vp, i64, dbl, vp],
+            "set_thermostat": [vp, dbl, dbl],
             "fire_minimize": [vp, vp, vp],
             "swap_sweep": [vp, i32, dbl, dbl, C.c_uint64, vp, vp, i64, C.POINTER(i64), vp],
             "get_info": [vp, vp],
@@ -245,6 +246,11 @@ def md_steps(h, nsteps, dt):
     return {k: getattr(t, k) for k, _ in Thermo._fields_}
 
 
+def set_thermostat(h, T_target, tau):
+    """Berendsen NVT for later md_steps (tau <= 0: back to NVE)."""
+    _check(lib().set_thermostat(h, float(T_target), float(tau)), h)
+
+
 def fire_minimize(h, raise_on_fail=False, **params):
     p = dict(FIRE_DEFAULTS)
     p.update(params)
@@ -328,6 +334,9 @@ class System:
 
     def md_steps(self, nsteps, dt):
         return md_steps(self.h, nsteps, dt)
+
+    def thermostat(self, T_target, tau):
+        set_thermostat(self.h, T_target, tau)
 
     def fire(self, **params):
         return fire_minimize(self.h, **params)
