@@ -255,6 +255,11 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return 0
 
+    # DRAM bytes per launch of the fused step kernel from one ncu capture of
+    # this kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum,
+    # cold L2 as ncu replays it); None where no capture of the current kernel
+    # exists for the workload
+    TRAFFIC = {"c1": 13155072 + 0}
     # roofline of the dominant kernel: fused force + kicks + drift (mixed)
     d = s.d
     RF = (d + 1 + 3) & ~3
@@ -280,7 +285,8 @@ def run_gpu(args):
         "fp64": fp64,
         "kernel_ms": prof,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": TRAFFIC.get(args.workload),
                      "kernel": "k_step<6,mixed> (pair forces + kicks + drift)",
                      "bytes_per_atom": bytes_per_atom, "peak_kind": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT,
