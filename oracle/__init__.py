@@ -22,6 +22,9 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   morse / law ........................ closed-form values of Eq. (1), the
                                        volume-scaled prefactors on two bodies
   sigma_eff .......................... Table III of the paper (4 digits)
+  observables ........................ uniform translation in closed form,
+                                       alpha2 -> 0 for Gaussian displacements,
+                                       Z on hypercubic lattices (2d, 2d^2)
   md_steps ........................... time reversibility, energy drift ~ dt^2,
                                        head-on two-body collision; Berendsen:
                                        ideal-gas relaxation in closed form
@@ -88,6 +91,8 @@ def _load():
             lib.orc_set_law.argtypes = [i32, dbl, i32]
             lib.orc_sigma_eff.restype = dbl
             lib.orc_sigma_eff.argtypes = [dbl, dbl, i64]
+            lib.orc_observables.restype = None
+            lib.orc_observables.argtypes = [i32, i64, dbl, vp, vp, vp, dbl, i32, dbl, vp, vp]
             lib.orc_harmonic.restype = dbl
             lib.orc_harmonic.argtypes = [dbl, dbl, dbl, C.POINTER(dbl)]
             lib.orc_forces.restype = None
@@ -256,6 +261,22 @@ def force_on(x, sigma, L, i, eps=1.0):
     e, w = C.c_double(), C.c_double()
     _load().orc_force_on(d, N, L, _p(x), _p(sigma), eps, int(i), _p(Fi), C.byref(e), C.byref(w))
     return Fi, e.value, w.value
+
+
+def observables(x, xref, sigma, L, a, nbins=0, r_max=1.0):
+    """dict(msd, mqd, alpha2, f_ov, Z[, G_s]) of unwrapped x against xref
+    (sigma None: Z is not computed)."""
+    x = _f64(x)
+    N, d = x.shape
+    out = np.zeros(5)
+    gs = np.zeros(max(nbins, 1))
+    sg = None if sigma is None else _f64(sigma)
+    _load().orc_observables(d, N, L, _p(x), _p(_f64(xref)), _p(sg), float(a),
+                            int(nbins), float(r_max), _p(out), _p(gs))
+    r = dict(msd=out[0], mqd=out[1], alpha2=out[2], f_ov=out[3], Z=out[4])
+    if nbins > 0:
+        r["G_s"] = gs[:nbins]
+    return r
 
 
 def kinetic(v, mass=None):

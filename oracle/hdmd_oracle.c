@@ -667,6 +667,55 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
 }
 
 /* ------------------------------------------------------------------ */
+/* observables (Sec. II.E)                                              */
+/* ------------------------------------------------------------------ */
+
+/* Against the reference configuration xref (both unwrapped, row-major):
+ *   out[0] = <|dr|^2>, out[1] = <|dr|^4>,
+ *   out[2] = alpha_2 = d <|dr|^4> / ((d + 2) <|dr|^2>^2) - 1  (Eq. (14)),
+ *   out[3] = f_ov = (1/N) sum_i Theta(a - |dr_i|), Theta(0) = 0 (Eq. (15)),
+ *   out[4] = Z = (1/N) sum_i #{j != i : r_ij < sigma_ij} at positions x
+ *            (minimum image), by brute force over all pairs (0 when sigma
+ *            is NULL);
+ * gs[b] (nbins > 0) = (1/N) sum_i [b w <= |dr_i| < (b+1) w] / w, w = r_max /
+ * nbins: the self part of the van Hove function (Eq. (16)) with its delta
+ * function smeared over bins of width w. */
+void orc_observables(int d, int64_t N, double L, const double *x, const double *xref,
+                     const double *sigma, double a, int nbins, double r_max,
+                     double *out, double *gs)
+{
+    double s2 = 0.0, s4 = 0.0, nov = 0.0, nz = 0.0;
+    double w = nbins > 0 ? r_max / nbins : 1.0;
+    for (int b = 0; b < nbins; ++b) gs[b] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double r2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double t = x[i * d + k] - xref[i * d + k];
+            r2 += t * t;
+        }
+        s2 += r2;
+        s4 += r2 * r2;
+        double r = sqrt(r2);
+        if (r < a) nov += 1.0;
+        if (nbins > 0 && r < r_max) {
+            int b = (int)floor(r / w);
+            if (b < nbins) gs[b] += 1.0;
+        }
+        for (int64_t j = 0; sigma && j < N; ++j) {
+            if (j == i) continue;
+            double sij = 0.5 * (sigma[i] + sigma[j]);
+            if (dist2(d, L, x, i, j) < sij * sij) nz += 1.0;
+        }
+    }
+    for (int b = 0; b < nbins; ++b) gs[b] /= (double)N * w;
+    out[0] = s2 / N;
+    out[1] = s4 / N;
+    out[2] = out[0] > 0.0 ? d * out[1] / ((d + 2.0) * out[0] * out[0]) - 1.0 : 0.0;
+    out[3] = nov / N;
+    out[4] = nz / N;
+}
+
+/* ------------------------------------------------------------------ */
 /* SWAP Monte Carlo                                                     */
 /* ------------------------------------------------------------------ */
 

@@ -510,3 +510,42 @@ def test_berendsen_with_tau_equal_dt_hits_the_target_in_one_step(orc):
     assert 2 * r["K"] / (d * (N - 1)) == pytest.approx(0.3, rel=1e-12)
     r0 = orc.md_steps(x, v, sigma, L, 1, 0.004, skin=2.0)       # NVE: unchanged
     assert r0["K"] == pytest.approx(orc.kinetic(v), rel=1e-14)
+
+
+# ------------------------------------------------------------------ observables (Sec. II.E)
+@pytest.mark.parametrize("d", [2, 3, 6])
+def test_observables_of_a_uniform_translation(orc, d):
+    """Every atom moved by the same vector c: msd = |c|^2, mqd = |c|^4,
+    alpha2 = d/(d+2) - 1, f_ov = [|c| < a], G_s one bin holding 1/w."""
+    rng = np.random.default_rng(d)
+    N, L = 200, 9.0
+    x0 = W.uniform_positions(rng, N, d, L)
+    c = rng.normal(size=d)
+    c *= 0.37 / np.linalg.norm(c)
+    sigma = np.full(N, 0.01)
+    for a, fov in ((0.5, 1.0), (0.3, 0.0)):
+        r = orc.observables(x0 + c, x0, sigma, L, a, nbins=10, r_max=1.0)
+        assert r["msd"] == pytest.approx(0.37 ** 2, rel=1e-13)
+        assert r["mqd"] == pytest.approx(0.37 ** 4, rel=1e-13)
+        assert r["alpha2"] == pytest.approx(d / (d + 2.0) - 1.0, abs=1e-12)
+        assert r["f_ov"] == fov
+        assert r["G_s"][3] == pytest.approx(1.0 / 0.1, rel=1e-12)
+        assert r["G_s"].sum() * 0.1 == pytest.approx(1.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_non_gaussian_parameter_vanishes_for_gaussian_displacements(orc, d):
+    rng = np.random.default_rng(10 + d)
+    N = 200000
+    x0 = np.zeros((N, d))
+    dx = rng.normal(scale=0.2, size=(N, d))
+    r = orc.observables(dx, x0, None, 1e6, 0.1)
+    assert abs(r["alpha2"]) < 0.02
+    assert r["msd"] == pytest.approx(d * 0.04, rel=0.01)
+
+
+@pytest.mark.parametrize("d,sig,expect", [(2, 1.05, 4), (3, 1.05, 6), (3, 1.45, 18), (4, 1.05, 8)])
+def test_coordination_on_lattices(orc, d, sig, expect):
+    x, L = W.lattice(d, 5)
+    r = orc.observables(x, x, np.full(len(x), sig), L, 0.1)
+    assert r["Z"] == expect
