@@ -406,6 +406,7 @@ def run_paper(args):
         with hdmd.System(d, s.L, s.sigma, x0, s.v, s.mass, skin=0.25, precision=hdmd.HDMD_MIXED,
                          stream=stream.cuda_stream, law="morse", a=W.MORSE_A, eps_scale=True) as g:
             g.md_steps(steps_per_tau, W.PAPER_DT)          # warm-up: graphs, first builds
+            g.set_reference()                                # r_i(0) of the observables
             a = torch.cuda.Event(enable_timing=True)
             c = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -419,13 +420,18 @@ def run_paper(args):
             c.synchronize()
             sec = a.elapsed_time(c) / 1000.0
             info = g.info()
+            t0 = time.perf_counter()
+            obs = g.observables(nbins=100, r_max=2.0)
+            obs_ms = 1000.0 * (time.perf_counter() - t0)
         n_steps = steps_per_tau * args.paper_tau
         z = info["total_list_entries"] / s.N
         rows.append({"d": d, "N": s.N, "phi_star": W.PHI_STAR[d], "L": s.L, "n_cell": info["n_cell"],
                      "seconds": sec, "atom_steps_per_s": s.N * n_steps / sec,
                      "ns_per_list_entry_step": 1e9 * sec / (n_steps * s.N * z),
                      "mean_list_length": z, "rebuilds": reb, "swap_accepted": acc,
-                     "T_end": t["T"], "E_pair_per_atom": t["E_pair"] / s.N})
+                     "T_end": t["T"], "E_pair_per_atom": t["E_pair"] / s.N,
+                     "msd": obs["msd"], "alpha2": obs["alpha2"], "f_ov": obs["f_ov"],
+                     "Z": obs["Z"], "observables_ms": obs_ms})
         total_atom_steps += s.N * n_steps
         total_s += sec
         print(json.dumps({"paper_row": rows[-1]}), file=sys.stderr, flush=True)

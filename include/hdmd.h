@@ -177,6 +177,31 @@ hdmd_status compute_forces(hdmd_system *sys, double *energy, double *virial);
  * lists and runs again. */
 hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last);
 
+/* Observables of Sec. II.E against a reference configuration (the paper's
+ * r_i(0), taken at step n_msdstart):
+ *   msd = <|dr|^2>, mqd = <|dr|^4> over the N atoms, dr = unwrapped
+ *   displacement since the reference;
+ *   alpha2 = d mqd / ((d + 2) msd^2) - 1, the non-Gaussian parameter (Eq. (14));
+ *   f_ov = fraction of atoms with |dr| < a, the overlap function (Eq. (15),
+ *   whose threshold is 0.1 d in units of the typical diameter);
+ *   Z = mean number of neighbours closer than sigma_ij (coordination number). */
+typedef struct {
+    double msd, mqd, alpha2, f_ov, Z;
+} hdmd_observables;
+
+/* Store the reference configuration: x_ref[N*d] (host, row-major, caller
+ * order, unwrapped) or, when NULL, the current unwrapped positions. */
+hdmd_status set_reference(hdmd_system *sys, const double *x_ref);
+
+/* Observables at the current positions against the stored reference
+ * (HDMD_E_INVALID without one).  a_ov: overlap threshold (<= 0: 0.1 d).
+ * gs (nullable, host [nbins]) receives the self part of the van Hove
+ * function (Eq. (16)) as a histogram: gs[b] = (atoms with b w <= |dr| <
+ * (b + 1) w) / (N w), w = r_max / nbins; nbins in 0..65536 (0: none),
+ * r_max > 0 when nbins > 0. */
+hdmd_status observables(hdmd_system *sys, double a_ov, int nbins, double r_max,
+                        hdmd_observables *out, double *gs);
+
 /* Berendsen thermostat (Berendsen et al. 1984; the NVT control of
  * Sec. II.E, which the paper applies inside the second kick of each step,
  * Sec. II.B).  With tau > 0 every later md_steps ends each step's second

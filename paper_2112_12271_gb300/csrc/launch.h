@@ -30,6 +30,12 @@ void launch_import_sigma(const Dev &dv, const double *sig, cudaStream_t s);
 // internal -> caller-order row-major (wrapped x, img, v, F, sigma); nullable outputs
 void launch_export(const Dev &dv, double *x_rm, int32_t *img_rm, double *v_rm, double *f_rm,
                    double *sig, cudaStream_t s);
+// observables (kernels_obs.cu): reference = current unwrapped positions in
+// caller order; displacement sums into dv.red[0..2], Z count into
+// dv.red[R_P], G_s counts into hist
+void launch_reference(const Dev &dv, double *ref, cudaStream_t s);
+void launch_observe(const Dev &dv, const double *ref, double a2, int nbins, double inv_w,
+                    unsigned int *hist, int want_z, cudaStream_t s);
 // the whole list build: wrap + bin + counting sort + reorder + Verlet lists.
 // buf: which gather buffer (0/1) receives the fresh rows; guarded: kernels
 // return at once unless flags->rebuild is set.

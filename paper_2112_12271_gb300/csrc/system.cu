@@ -121,6 +121,9 @@ struct hdmd_system {
     std::string graph_err;
     double sigma_max = 0;
     double nvt_T = 0.0, nvt_tau = 0.0;   // Berendsen thermostat (tau <= 0: NVE)
+    double *obs_ref = nullptr;         // reference positions [N][d], caller order
+    unsigned int *obs_hist = nullptr;  // G_s counts
+    int obs_hist_cap = 0;
     bool unit_mass = true;
     double *inv_mass_store = nullptr;
     double *st_f = nullptr;
@@ -1449,6 +1452,75 @@ hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_ou
     return build_forced(sys, buf0);
 }
 
+hdmd_status set_reference(hdmd_system *sys, const double *x_ref) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    const size_t n = (size_t)sys->N * sys->d;
+    if (x_ref)
+        for (size_t a = 0; a < n; ++a)
+            if (!std::isfinite(x_ref[a])) return fail(sys, HDMD_E_INVALID, "non-finite reference position");
+    if (!sys->obs_ref) {
+        void *q = nullptr;
+        if (pool_alloc(&q, sizeof(double) * n, sys->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(sys, HDMD_E_NOMEM, "reference positions");
+        }
+        sys->obs_ref = (double *)q;
+    }
+    if (x_ref) {
+        CK(cudaMemcpyAsync(sys->obs_ref, x_ref, sizeof(double) * n, cudaMemcpyHostToDevice, sys->stream));
+    } else {
+        launch_reference(sys->dv, sys->obs_ref, sys->stream);
+        CKL(sys);
+    }
+    CK(cudaStreamSynchronize(sys->stream));
+    return HDMD_OK;
+}
+
+hdmd_status observables(hdmd_system *sys, double a_ov, int nbins, double r_max,
+                        hdmd_observables *out, double *gs) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!out) return fail(sys, HDMD_E_INVALID, "out is NULL");
+    if (!sys->obs_ref) return fail(sys, HDMD_E_INVALID, "no reference configuration (set_reference)");
+    if (nbins < 0 || nbins > 65536) return fail(sys, HDMD_E_INVALID, "nbins must be in 0..65536");
+    if (nbins > 0 && (!(r_max > 0.0) || !std::isfinite(r_max)))
+        return fail(sys, HDMD_E_INVALID, "r_max must be positive");
+    if (!std::isfinite(a_ov)) return fail(sys, HDMD_E_INVALID, "a_ov must be finite");
+    const double a = a_ov > 0.0 ? a_ov : 0.1 * sys->d;
+    if (nbins > sys->obs_hist_cap) {
+        pool_free(sys->obs_hist, sys->stream);
+        sys->obs_hist = nullptr;
+        sys->obs_hist_cap = 0;
+        void *q = nullptr;
+        if (pool_alloc(&q, sizeof(unsigned int) * nbins, sys->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(sys, HDMD_E_NOMEM, "G_s histogram");
+        }
+        sys->obs_hist = (unsigned int *)q;
+        sys->obs_hist_cap = nbins;
+    }
+    if (nbins > 0) CK(cudaMemsetAsync(sys->obs_hist, 0, sizeof(unsigned int) * nbins, sys->stream));
+    const double w = nbins > 0 ? r_max / nbins : 1.0;
+    launch_observe(sys->dv, sys->obs_ref, a * a, nbins, 1.0 / w, sys->obs_hist, 1, sys->stream);
+    CKL(sys);
+    std::vector<unsigned int> h((size_t)std::max(nbins, 1));
+    if (nbins > 0)
+        CK(cudaMemcpyAsync(h.data(), sys->obs_hist, sizeof(unsigned int) * nbins, cudaMemcpyDeviceToHost,
+                           sys->stream));
+    st = read_flags(sys);
+    if (st) return st;
+    const double N = (double)sys->N, d = (double)sys->d;
+    out->msd = sys->h_red[0] / N;
+    out->mqd = sys->h_red[1] / N;
+    out->alpha2 = out->msd > 0.0 ? d * out->mqd / ((d + 2.0) * out->msd * out->msd) - 1.0 : 0.0;
+    out->f_ov = sys->h_red[2] / N;
+    out->Z = sys->h_red[R_P] / N;
+    if (gs)
+        for (int b = 0; b < nbins; ++b) gs[b] = (double)h[b] / (N * w);
+    return HDMD_OK;
+}
+
 hdmd_status set_thermostat(hdmd_system *sys, double T_target, double tau) {
     hdmd_status st = validate_sys(sys);
     if (st) return st;
@@ -1508,6 +1580,8 @@ hdmd_status destroy_system(hdmd_system *sys) {
     pool_free(sys->nbr, sys->stream);
     pool_free(sys->code, sys->stream);
     pool_free(sys->st_idx, sys->stream);
+    pool_free(sys->obs_ref, sys->stream);
+    pool_free(sys->obs_hist, sys->stream);
     pinned_put(sys->h_flags);
     pinned_put(sys->h_red);
     if (sys->cap_stream) cudaStreamDestroy(sys->cap_stream);

@@ -113,6 +113,8 @@ def lib():
             "compute_forces": [vp, C.POINTER(dbl), C.POINTER(dbl)],
             "md_steps": [vp, i64, dbl, vp],
             "set_thermostat": [vp, dbl, dbl],
+            "set_reference": [vp, vp],
+            "observables": [vp, dbl, i32, dbl, vp, vp],
             "fire_minimize": [vp, vp, vp],
             "swap_sweep": [vp, i32, dbl, dbl, C.c_uint64, vp, vp, i64, C.POINTER(i64), vp],
             "get_info": [vp, vp],
@@ -246,6 +248,28 @@ def md_steps(h, nsteps, dt):
     return {k: getattr(t, k) for k, _ in Thermo._fields_}
 
 
+class Observables(C.Structure):
+    _fields_ = [("msd", C.c_double), ("mqd", C.c_double), ("alpha2", C.c_double),
+                ("f_ov", C.c_double), ("Z", C.c_double)]
+
+
+def set_reference(h, x_ref=None):
+    """Reference configuration for the observables (None: current positions)."""
+    _check(lib().set_reference(h, _p(None if x_ref is None else _f64(x_ref))), h)
+
+
+def observables(h, a_ov=0.0, nbins=0, r_max=0.0):
+    """dict(msd, mqd, alpha2, f_ov, Z) and, with nbins > 0, the G_s histogram."""
+    o = Observables()
+    gs = np.zeros(max(nbins, 1))
+    _check(lib().observables(h, float(a_ov), int(nbins), float(r_max), C.byref(o),
+                             _p(gs) if nbins > 0 else None), h)
+    out = {k: getattr(o, k) for k, _ in Observables._fields_}
+    if nbins > 0:
+        out["G_s"] = gs[:nbins]
+    return out
+
+
 def set_thermostat(h, T_target, tau):
     """Berendsen NVT for later md_steps (tau <= 0: back to NVE)."""
     _check(lib().set_thermostat(h, float(T_target), float(tau)), h)
@@ -337,6 +361,12 @@ class System:
 
     def thermostat(self, T_target, tau):
         set_thermostat(self.h, T_target, tau)
+
+    def set_reference(self, x_ref=None):
+        set_reference(self.h, x_ref)
+
+    def observables(self, a_ov=0.0, nbins=0, r_max=0.0):
+        return observables(self.h, a_ov, nbins, r_max)
 
     def fire(self, **params):
         return fire_minimize(self.h, **params)

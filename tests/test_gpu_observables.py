@@ -1,0 +1,61 @@
+"""GPU parity of the on-device observables (Sec. II.E) against the oracle:
+after MD from a stored reference, MSD, MQD and alpha2 (Eq. (14)) within
+1e-10 relative (FP64 displacement sums in another order), f_ov (Eq. (15)),
+the G_s histogram (Eq. (16)) and the coordination number Z exactly (atoms
+within 1e-9 of a bin edge or of the threshold excepted, none occur here)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_12271_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2112_12271_gb300 import build, hdmd
+    build.build()
+    oracle.build()
+    return hdmd
+
+
+@pytest.mark.parametrize("d,N,phi", [(3, 1500, 0.55), (6, 2000, 0.12)])
+def test_observables_match_oracle(H, d, N, phi):
+    s = W.make_system(d, N, phi=phi, dist="poly", T=0.05, seed=d)
+    for prec in (H.HDMD_FP64, H.HDMD_MIXED):
+        with H.System(d, s.L, s.sigma, s.x, s.v, precision=prec) as g:
+            st0 = g.state()
+            x0u = st0["x"] + s.L * st0["img"]
+            g.set_reference()
+            g.md_steps(400, 0.005)
+            st = g.state()
+            xu = st["x"] + s.L * st["img"]
+            got = g.observables(a_ov=0.0, nbins=40, r_max=0.4)
+            got2 = g.observables(a_ov=0.05)
+        ref = oracle.observables(xu, x0u, s.sigma, s.L, 0.1 * d, nbins=40, r_max=0.4)
+        ref2 = oracle.observables(xu, x0u, None, s.L, 0.05)
+        assert ref["msd"] > 0
+        for k in ("msd", "mqd", "alpha2"):
+            assert got[k] == pytest.approx(ref[k], rel=1e-10, abs=1e-14), k
+        assert got["f_ov"] == ref["f_ov"] and got2["f_ov"] == ref2["f_ov"]
+        assert np.array_equal(got["G_s"], ref["G_s"])
+        assert got["Z"] == ref["Z"] and got["Z"] > 0
+
+
+def test_explicit_reference_and_errors(H):
+    s = W.make_system(4, 800, phi=0.3, dist="poly", T=0.01, seed=2)
+    with H.System(4, s.L, s.sigma, s.x, s.v, precision=H.HDMD_FP64) as g:
+        with pytest.raises(H.HDMDError):
+            g.observables()                       # no reference yet
+        shift = np.full(4, 0.25)
+        g.set_reference(s.x - shift)              # every atom 0.5 from it
+        r = g.observables(a_ov=0.6)
+        assert r["msd"] == pytest.approx(4 * 0.25 ** 2, rel=1e-12)
+        assert r["alpha2"] == pytest.approx(4 / 6 - 1, abs=1e-12)
+        assert r["f_ov"] == 1.0
+        with pytest.raises(H.HDMDError):
+            g.observables(nbins=10, r_max=0.0)
