@@ -19,6 +19,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   forces ............................. two-body closed form, central finite
                                        differences of E, Newton's third law,
                                        virial = -sum x.grad U (both laws)
+  mie ................................ the textbook WCA form for n = 6,
+                                       closed-form values for other n
   morse / law ........................ closed-form values of Eq. (1), the
                                        volume-scaled prefactors on two bodies
   sigma_eff .......................... Table III of the paper (4 digits)
@@ -87,6 +89,8 @@ def _load():
                                          C.POINTER(dbl), C.POINTER(dbl)]
             lib.orc_morse.restype = dbl
             lib.orc_morse.argtypes = [dbl, dbl, dbl, dbl, C.POINTER(dbl)]
+            lib.orc_mie.restype = dbl
+            lib.orc_mie.argtypes = [dbl, dbl, dbl, i32, C.POINTER(dbl)]
             lib.orc_set_law.restype = i32
             lib.orc_set_law.argtypes = [i32, dbl, i32]
             lib.orc_sigma_eff.restype = dbl
@@ -207,6 +211,13 @@ def morse(r: float, s: float, eps: float = 1.0, a: float = 30.0):
     return u, fr.value
 
 
+def mie(r: float, s: float, eps: float = 1.0, n: int = 6):
+    """(U, |f|/r) of the Mie law truncated at r = s and shifted (Sec. II.A)."""
+    fr = C.c_double()
+    u = _load().orc_mie(r, s, eps, int(n), C.byref(fr))
+    return u, fr.value
+
+
 def sigma_eff(a: float, T: float, npts: int = 200000) -> float:
     """Effective hard-sphere diameter of the Morse law, Eq. (12)."""
     return _load().orc_sigma_eff(a, T, npts)
@@ -214,13 +225,14 @@ def sigma_eff(a: float, T: float, npts: int = 200000) -> float:
 
 class law:
     """Context manager selecting the pair law of every oracle routine:
-    kind "harmonic" or "morse" (stiffness a), eps_scale for the volume-scaled
+    kind "harmonic", "morse" (stiffness a) or "mie" (exponent n = a),
+    eps_scale for the volume-scaled
     prefactors eps_i = eps sigma_i^d mixed as sqrt(eps_i eps_j).  The setting
     is process-wide while the block runs; the harmonic law with one eps is
     restored on exit."""
 
     def __init__(self, kind="harmonic", a=30.0, eps_scale=False):
-        self.args = ({"harmonic": 0, "morse": 1}[kind], float(a), int(bool(eps_scale)))
+        self.args = ({"harmonic": 0, "morse": 1, "mie": 2}[kind], float(a), int(bool(eps_scale)))
 
     def __enter__(self):
         if _load().orc_set_law(*self.args) != 0:

@@ -299,9 +299,22 @@ double orc_morse(double r, double s, double eps, double a, double *fr)
     return eps * (e2 - 2.0 * e1 + 1.0);
 }
 
+/* The Mie law of Sec. II.A, U = eps [(s/r)^(2n) - 2 (s/r)^n], truncated at
+ * its minimum r = s (the cut of the paper's stock code) and shifted by +eps
+ * so that it is continuous there: U = eps [(s/r)^(2n) - 2 (s/r)^n + 1] for
+ * r < s, 0 beyond (for n = 6 the WCA form of Lennard-Jones).  Force on i
+ * from j: -dU/dr = (2n eps / r) [(s/r)^(2n) - (s/r)^n] along (x_i - x_j)/r. */
+double orc_mie(double r, double s, double eps, int n, double *fr)
+{
+    if (r >= s) { *fr = 0.0; return 0.0; }
+    double q = pow(s / r, n);
+    *fr = 2.0 * n * eps * (q * q - q) / (r * r);
+    return eps * (q * q - 2.0 * q + 1.0);
+}
+
 /* The pair law every routine below applies, set process-wide (default:
  * harmonic, one eps for all pairs).  kind 0 = harmonic, 1 = Morse with
- * stiffness a.  eps_scale = 1 gives atom i the prefactor
+ * stiffness a, 2 = Mie with exponent n = (int)a.  eps_scale = 1 gives atom i the prefactor
  * eps_i = eps sigma_i^d (Sec. II.A: prefactors scale with particle volume)
  * and a pair eps_ij = sqrt(eps_i eps_j) (the mixing rule of Sec. II.A);
  * eps_scale = 0 gives every pair eps.  Returns 0, or -1 for a bad kind. */
@@ -311,7 +324,7 @@ static int g_law_eps_scale = 0;
 
 int orc_set_law(int kind, double a, int eps_scale)
 {
-    if (kind != 0 && kind != 1) return -1;
+    if (kind < 0 || kind > 2) return -1;
     g_law_kind = kind;
     g_law_a = a;
     g_law_eps_scale = eps_scale ? 1 : 0;
@@ -326,6 +339,7 @@ static double pair_law(int d, double r, double si, double sj, double eps, double
     double e = eps;
     if (g_law_eps_scale) e = sqrt((eps * pow(si, d)) * (eps * pow(sj, d)));
     if (g_law_kind == 1) return orc_morse(r, s, e, g_law_a, fr);
+    if (g_law_kind == 2) return orc_mie(r, s, e, (int)g_law_a, fr);
     return orc_harmonic(r, s, e, fr);
 }
 

@@ -549,3 +549,31 @@ def test_coordination_on_lattices(orc, d, sig, expect):
     x, L = W.lattice(d, 5)
     r = orc.observables(x, x, np.full(len(x), sig), L, 0.1)
     assert r["Z"] == expect
+
+
+# ------------------------------------------------------------------ Mie law (Sec. II.A)
+def test_mie_n6_is_the_wca_form(orc):
+    """For n = 6 the truncated and shifted Mie law is WCA: 4 eps [(s'/r)^12 -
+    (s'/r)^6] + eps for r < 2^(1/6) s' with s' = s 2^(-1/6)."""
+    eps, s = 0.8, 1.1
+    sp = s * 2.0 ** (-1.0 / 6.0)
+    for r in (0.7, 0.95, 1.05, 1.0999):
+        u, fr = orc.mie(r, s, eps, 6)
+        lj = 4 * eps * ((sp / r) ** 12 - (sp / r) ** 6) + eps
+        flj = 4 * eps * (12 * sp ** 12 / r ** 13 - 6 * sp ** 6 / r ** 7)
+        assert u == pytest.approx(lj, rel=1e-12, abs=1e-15)
+        assert fr * r == pytest.approx(flj, rel=1e-12, abs=1e-15)
+    assert orc.mie(1.1, s, eps, 6) == (0.0, 0.0)
+
+
+@pytest.mark.parametrize("n", [3, 8, 12])
+def test_mie_closed_forms_and_gradient(orc, n):
+    eps, s = 1.3, 0.9
+    r = s * 2.0 ** (-1.0 / n)                   # (s/r)^n = 2
+    u, fr = orc.mie(r, s, eps, n)
+    assert u == pytest.approx(eps, rel=1e-13)   # eps (4 - 4 + 1)
+    assert fr * r * r == pytest.approx(4 * n * eps, rel=1e-13)
+    h = 1e-6
+    for r in (0.6, 0.8, 0.89):
+        fd = -(orc.mie(r + h, s, eps, n)[0] - orc.mie(r - h, s, eps, n)[0]) / (2 * h)
+        assert fd == pytest.approx(orc.mie(r, s, eps, n)[1] * r, rel=1e-6)
