@@ -55,11 +55,16 @@ typedef enum { HDMD_FP64 = 0, HDMD_MIXED = 1 } hdmd_precision;
  *   kind 1: the paper's truncated and shifted Morse law, Eq. (1),
  *     U(r) = eps_ij [exp(-2a(r - sigma_ij)) - 2 exp(-a(r - sigma_ij)) + 1]
  *     for r < sigma_ij, 0 beyond (a > 0: stiffness; the paper uses 30).
+ *   kind 2: the Mie law of Sec. II.A truncated at its minimum sigma_ij (the
+ *     paper's default cut) and shifted to be continuous there,
+ *     U(r) = eps_ij [(sigma_ij/r)^(2n) - 2 (sigma_ij/r)^n + 1] for
+ *     r < sigma_ij, 0 beyond (n = n_mie in 1..24; n = 6 is the WCA form).
  * eps_scale 0: eps_ij = eps for every pair; 1: each atom has the prefactor
  * eps_i = eps sigma_i^d (prefactors scale with particle volume, Sec. II.A)
  * and eps_ij = sqrt(eps_i eps_j) (the mixing rule of Sec. II.A).
  * skin: the Verlet-list skin s of Sec. II.C (list radius sigma_ij + s).
- * Other kinds, a <= 0 for kind 1, or eps_scale outside {0, 1} are rejected
+ * Other kinds, a <= 0 for kind 1, n_mie outside 1..24 for kind 2, or
+ * eps_scale outside {0, 1} are rejected
  * with HDMD_E_INVALID.  The batched engine and the allocation-free force
  * call use kind 0 with one eps. */
 typedef struct {
@@ -68,6 +73,7 @@ typedef struct {
     double skin;
     double a;
     int eps_scale;
+    int n_mie;
 } hdmd_potential;
 
 /* Thermodynamic summary (Sec. II.E): pair energy E = sum_{i<j} U_ij, virial

@@ -82,9 +82,10 @@ struct Dev {
     int d, N, Npad, G, cap;
     int lgG;        // log2(G)
     double L, halfL, invL, skin, eps;
-    int law;        // 0 harmonic, 1 Morse (Eq. (1))
+    int law;        // 0 harmonic, 1 Morse (Eq. (1)), 2 Mie (truncated, shifted)
     int eps_scale;  // 1: eps_ij = eps (sigma_i sigma_j)^(d/2)
     double morse_a; // Morse stiffness
+    int mie_n;      // Mie exponent (law 2)
     int n;          // subcells per axis
     int ncells;
     double Lsc, invLsc;

@@ -7,7 +7,9 @@
 // which keeps its digits near r = s), force on i = 2 a e (m + 1) m
 // (x_i - x_j)/r.  e = eps_ij: eps, or with volume-scaled prefactors
 // eps (sigma_i sigma_j)^(d/2) = sqrt(eps_i eps_j), eps_i = eps sigma_i^d
-// (Sec. II.A), from the radii sigma/2 held in the rows.
+// (Sec. II.A), from the radii sigma/2 held in the rows.  LAW 2, the Mie law
+// truncated at its minimum s and shifted: U = e [(s/r)^2n - 2 (s/r)^n + 1]
+// = e (q - 1)^2 with q = (s/r)^n, force on i = 2 n e (q^2 - q) (x_i - x_j)/r^2.
 // Lane g of the atom's group of G = 1 << lgG lanes walks entries g, g+G, ...
 // and accumulates its share into f, e (sum of U) and w (sum of r.f); the
 // caller combines the lanes.  FP64P selects FP64 pair arithmetic on the
@@ -21,6 +23,18 @@
 #endif
 
 namespace hdmd {
+
+// q^n for a small non-negative integer n (binary powering)
+template <typename T>
+__device__ __forceinline__ T powi(T q, int n) {
+    T r = T(1);
+    while (n) {
+        if (n & 1) r *= q;
+        q *= q;
+        n >>= 1;
+    }
+    return r;
+}
 
 // pair prefactor from the radii hi, hj: eps, or eps (4 hi hj)^(D/2)
 template <int D, typename T>
@@ -69,6 +83,10 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
                     const double gg = 1.0 - r / s;
                     fr = r > 0.0 ? (ee / s) * gg / r : 0.0;
                     u = 0.5 * ee * gg * gg;
+                } else if constexpr (LAW == 2) {
+                    const double q = powi(s / r, dv.mie_n);
+                    fr = r > 0.0 ? 2.0 * dv.mie_n * ee * (q * q - q) / r2 : 0.0;
+                    u = ee * (q - 1.0) * (q - 1.0);
                 } else {
                     const double m = expm1(-dv.morse_a * (r - s));
                     fr = r > 0.0 ? 2.0 * dv.morse_a * ee * (m + 1.0) * m / r : 0.0;
@@ -132,7 +150,14 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
                     const float rinv = rsqrtf(r2);
                     const float r = r2 * rinv;
                     const float ee = eps_pair<D, float>(eps, hi, rj[u][D], scale);
-                    if constexpr (LAW == 0) {
+                    if constexpr (LAW == 2) {
+                        const float q = powi(s * rinv, dv.mie_n);
+                        const float fr = 2.f * (float)dv.mie_n * ee * (q * q - q) * rinv * rinv;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+                        e = (FT)fmaf(ee * (q - 1.f), q - 1.f, (float)e);
+                        w = (FT)fmaf(fr, r2, (float)w);
+                    } else if constexpr (LAW == 0) {
                         const float inv_s = __frcp_rn(s);
                         const float gg = fmaf(-r, inv_s, 1.f);
                         const float fr = ee * inv_s * gg * rinv;

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
         FT e = 0, w = 0;
         if (valid) {
             if (dv.law == 1) pair_forces<D, FP64P, FT, 1>(dv, i, g, lgG, cfg.in_buf, f, e, w);
+            else if (dv.law == 2) pair_forces<D, FP64P, FT, 2>(dv, i, g, lgG, cfg.in_buf, f, e, w);
             else pair_forces<D, FP64P, FT, 0>(dv, i, g, lgG, cfg.in_buf, f, e, w);
         }
         for (int o = G >> 1; o > 0; o >>= 1) {

@@ -171,6 +171,12 @@ __device__ __forceinline__ double pair_u(const Dev &dv, double r, double si, dou
         const double m = expm1(-dv.morse_a * (r - s));
         return e * m * m;
     }
+    if (dv.law == 2) {
+        double q = 1.0, b = s / r;
+        for (int n = dv.mie_n; n; n >>= 1, b *= b)
+            if (n & 1) q *= b;
+        return e * (q - 1.0) * (q - 1.0);
+    }
     const double g = 1.0 - r / s;
     return 0.5 * e * g * g;
 }

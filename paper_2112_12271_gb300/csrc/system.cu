@@ -742,10 +742,11 @@ hdmd_status fire_once(hdmd_system *sys, const hdmd_fire_params &p, hdmd_fire_res
     fs[FP_FTOL] = p.f_tol;
     // FP32 pair forces resolve max|F| down to about (pair stiffness) x (FP32
     // position resolution): the switch threshold scales with the law's
-    // stiffness at contact relative to the harmonic law's, 1 (harmonic) or
-    // 2 (a sigma_max)^2 (Morse, Eq. (1))
+    // stiffness at contact relative to the harmonic law's, 1 (harmonic),
+    // 2 (a sigma_max)^2 (Morse, Eq. (1)) or 2 n^2 (Mie)
     const double stiff = sys->dv.law == 1 ? 2.0 * (sys->dv.morse_a * sys->sigma_max) *
                                                 (sys->dv.morse_a * sys->sigma_max)
+                       : sys->dv.law == 2 ? 2.0 * sys->dv.mie_n * sys->dv.mie_n
                                           : 1.0;
     fs[FP_SWITCH] = (mixed && p.polish_tol > p.f_tol) ? p.polish_tol * stiff : 0.0;
     fs[FP_NDELAY] = (double)p.n_delay;
@@ -924,8 +925,10 @@ hdmd_status check_create_args(int d, int64_t N, double L, const double *diameter
     if (!(L > 0.0) || !std::isfinite(L)) return fail(nullptr, HDMD_E_INVALID, "L must be positive and finite");
     if (!diameters) return fail(nullptr, HDMD_E_INVALID, "diameters is NULL");
     if (!pot) return fail(nullptr, HDMD_E_INVALID, "potential is NULL");
-    if (pot->kind != 0 && pot->kind != 1)
-        return fail(nullptr, HDMD_E_INVALID, "pair law kind must be 0 (harmonic) or 1 (Morse)");
+    if (pot->kind < 0 || pot->kind > 2)
+        return fail(nullptr, HDMD_E_INVALID, "pair law kind must be 0 (harmonic), 1 (Morse) or 2 (Mie)");
+    if (pot->kind == 2 && (pot->n_mie < 1 || pot->n_mie > 24))
+        return fail(nullptr, HDMD_E_INVALID, "the Mie exponent n_mie must be in 1..24");
     if (pot->kind == 1 && (!(pot->a > 0.0) || !std::isfinite(pot->a)))
         return fail(nullptr, HDMD_E_INVALID, "the Morse stiffness a must be positive and finite");
     if (pot->eps_scale != 0 && pot->eps_scale != 1)
@@ -1041,6 +1044,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     dv.law = pot->kind;
     dv.eps_scale = pot->eps_scale;
     dv.morse_a = pot->kind == 1 ? pot->a : 0.0;
+    dv.mie_n = pot->kind == 2 ? pot->n_mie : 0;
     dv.n = n;
     dv.ncells = 1;
     for (int k = 0; k < d; ++k) dv.ncells *= n;

@@ -31,16 +31,17 @@ class HDMDError(RuntimeError):
 
 class Potential(C.Structure):
     _fields_ = [("kind", C.c_int), ("eps", C.c_double), ("skin", C.c_double),
-                ("a", C.c_double), ("eps_scale", C.c_int)]
+                ("a", C.c_double), ("eps_scale", C.c_int), ("n_mie", C.c_int)]
 
 
-LAWS = {"harmonic": 0, "morse": 1}
+LAWS = {"harmonic": 0, "morse": 1, "mie": 2}
 
 
-def potential(eps=1.0, skin=0.3, law="harmonic", a=30.0, eps_scale=False):
-    """The pair law of include/hdmd.h: harmonic or the Morse law of Eq. (1)
-    (stiffness a), one eps or volume-scaled prefactors eps sigma_i^d."""
-    return Potential(LAWS[law], float(eps), float(skin), float(a), int(bool(eps_scale)))
+def potential(eps=1.0, skin=0.3, law="harmonic", a=30.0, eps_scale=False, n=6):
+    """The pair law of include/hdmd.h: harmonic, the Morse law of Eq. (1)
+    (stiffness a) or the truncated and shifted Mie law (exponent n); one eps
+    or volume-scaled prefactors eps sigma_i^d."""
+    return Potential(LAWS[law], float(eps), float(skin), float(a), int(bool(eps_scale)), int(n))
 
 
 class Thermo(C.Structure):
@@ -172,11 +173,11 @@ def default_stream():
 
 # ------------------------------------------------------------------ ABI calls
 def create_system(d, N, L, diameters, eps=1.0, skin=0.3, precision=HDMD_MIXED, stream=None,
-                  law="harmonic", a=30.0, eps_scale=False):
+                  law="harmonic", a=30.0, eps_scale=False, n=6):
     diam = _f64(diameters)
     if diam.shape != (N,):
         raise ValueError("diameters must have shape (N,)")
-    pot = potential(eps, skin, law, a, eps_scale)
+    pot = potential(eps, skin, law, a, eps_scale, n)
     h = C.c_void_p()
     st = lib().create_system(d, N, L, _p(diam), C.byref(pot), int(precision),
                              stream if stream is not None else default_stream(), C.byref(h))
@@ -185,12 +186,12 @@ def create_system(d, N, L, diameters, eps=1.0, skin=0.3, precision=HDMD_MIXED, s
 
 
 def system_footprint(d, N, L, diameters, eps=1.0, skin=0.3, precision=HDMD_MIXED,
-                     law="harmonic", a=30.0, eps_scale=False):
+                     law="harmonic", a=30.0, eps_scale=False, n=6):
     """Device bytes create_system would allocate (no device work)."""
     diam = _f64(diameters)
     if diam.shape != (N,):
         raise ValueError("diameters must have shape (N,)")
-    pot = potential(eps, skin, law, a, eps_scale)
+    pot = potential(eps, skin, law, a, eps_scale, n)
     b = C.c_int64(0)
     _check(lib().system_footprint(d, N, L, _p(diam), C.byref(pot), int(precision), C.byref(b)))
     return b.value
@@ -328,11 +329,12 @@ class System:
     """One resident system: the ABI calls bound to a handle."""
 
     def __init__(self, d, L, diameters, x=None, v=None, masses=None, eps=1.0, skin=0.3,
-                 precision=HDMD_MIXED, stream=None, law="harmonic", a=30.0, eps_scale=False):
+                 precision=HDMD_MIXED, stream=None, law="harmonic", a=30.0, eps_scale=False,
+                 n=6):
         self.d, self.L = int(d), float(L)
         self.N = int(np.asarray(diameters).shape[0])
         self.h = create_system(self.d, self.N, self.L, diameters, eps, skin, precision, stream,
-                               law, a, eps_scale)
+                               law, a, eps_scale, n)
         if x is not None:
             self.set_state(x, v, masses)
 
