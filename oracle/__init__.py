@@ -30,6 +30,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   md_steps ........................... time reversibility, energy drift ~ dt^2,
                                        head-on two-body collision; Berendsen:
                                        ideal-gas relaxation in closed form
+  md_npt ............................. ideal-gas volume relaxation in closed
+                                       form
   fire ............................... |F|max < 1e-10, E -> 0 below jamming,
                                        two spheres relax to contact
   swap ............................... brute dE, equal diameters always
@@ -107,6 +109,9 @@ def _load():
             lib.orc_md_steps.restype = i64
             lib.orc_md_steps.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl,
                                          dbl, i64, vp, i32, vp, dbl, dbl]
+            lib.orc_md_npt.restype = i64
+            lib.orc_md_npt.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, dbl, dbl, i64,
+                                       dbl, dbl, dbl, dbl, dbl, i64, vp, vp]
             lib.orc_fire.restype = i32
             lib.orc_fire.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl, vp,
                                      vp, vp]
@@ -316,6 +321,27 @@ def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None,
                              dt, int(nsteps), _p(F), int(have_F), _p(th), float(T_target),
                              float(tau))
     return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b))
+
+
+def md_npt(x, v, sigma, L, nsteps, dt, P_target, tau_P, beta, n_baro, skin=0.3, eps=1.0,
+           mass=None, img=None, T_target=0.0, tau=0.0, count=0):
+    """NPT with the Berendsen barostat on copies: dict(x, v, img, L, E, W, K,
+    rescales, count)."""
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    N, d = x.shape
+    m = None if mass is None else _f64(mass)
+    img = np.zeros((N, d), dtype=np.int32) if img is None else np.array(img, dtype=np.int32)
+    Lb = np.array([float(L)])
+    cnt = np.array([int(count)], dtype=np.int64)
+    th = np.zeros(3)
+    n = _load().orc_md_npt(d, N, _p(Lb), _p(x), _p(v), _p(img), _p(_f64(sigma)), _p(m), eps,
+                           skin, dt, int(nsteps), float(T_target), float(tau), float(P_target),
+                           float(tau_P), float(beta), int(n_baro), _p(cnt), _p(th))
+    if n < 0:
+        raise ValueError("barostat step would make the box vanish")
+    return dict(x=x, v=v, img=img, L=float(Lb[0]), E=th[0], W=th[1], K=th[2], rescales=int(n),
+                count=int(cnt[0]))
 
 
 FIRE_DEFAULTS = dict(dt0=0.005, dt_max=0.05, dt_min=1e-4, f_inc=1.1, f_dec=0.5,

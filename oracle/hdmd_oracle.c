@@ -680,6 +680,52 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
     return status;
 }
 
+/* NPT with the Berendsen barostat (Berendsen et al. 1984; Sec. II.E):
+ * nsteps of orc_md_steps (NVE, or NVT when tau > 0) in pieces of n_baro
+ * steps; after each full piece the pressure P = (2K + W)/(d L^d) of its end
+ * state gives mu = [1 - beta (n_baro dt / tau_P)(P_target - P)]^(1/d), and
+ * every position and the box side are multiplied by mu (the box stays
+ * centred at the origin).  *count carries the steps since the last rescale
+ * across calls.  *L is updated.  thermo as orc_md_steps, for the end state
+ * (after a final rescale, at the rescaled positions).  Returns the number of
+ * rescales, or -1 if one would make the box vanish. */
+int64_t orc_md_npt(int d, int64_t N, double *L, double *x, double *v, int32_t *img,
+                   const double *sigma, const double *mass, double eps, double skin,
+                   double dt, int64_t nsteps, double T_target, double tau,
+                   double P_target, double tau_P, double beta, int64_t n_baro,
+                   int64_t *count, double *thermo)
+{
+    double *F = (double *)malloc(sizeof(double) * (size_t)(N * d));
+    int64_t left = nsteps, nresc = 0;
+    int rescaled_last = 0;
+    thermo[0] = thermo[1] = thermo[2] = 0.0;
+    while (left > 0) {
+        int64_t chunk = n_baro - *count;
+        if (chunk > left) chunk = left;
+        orc_md_steps(d, N, *L, x, v, img, sigma, mass, eps, skin, dt, chunk, F, 0, thermo,
+                     T_target, tau);
+        left -= chunk;
+        *count += chunk;
+        rescaled_last = 0;
+        if (*count == n_baro) {
+            double V = pow(*L, d);
+            double P = (2.0 * thermo[2] + thermo[1]) / (d * V);
+            double base = 1.0 - beta * ((double)n_baro * dt / tau_P) * (P_target - P);
+            if (!(base > 0.0)) { free(F); return -1; }
+            double mu = pow(base, 1.0 / d);
+            for (int64_t a = 0; a < N * d; ++a) x[a] *= mu;
+            *L *= mu;
+            *count = 0;
+            ++nresc;
+            rescaled_last = 1;
+        }
+    }
+    if (rescaled_last) orc_md_steps(d, N, *L, x, v, img, sigma, mass, eps, skin, dt, 0, F, 0,
+                                    thermo, T_target, tau);
+    free(F);
+    return nresc;
+}
+
 /* ------------------------------------------------------------------ */
 /* observables (Sec. II.E)                                              */
 /* ------------------------------------------------------------------ */

@@ -577,3 +577,20 @@ def test_mie_closed_forms_and_gradient(orc, n):
     for r in (0.6, 0.8, 0.89):
         fd = -(orc.mie(r + h, s, eps, n)[0] - orc.mie(r - h, s, eps, n)[0]) / (2 * h)
         assert fd == pytest.approx(orc.mie(r, s, eps, n)[1] * r, rel=1e-6)
+
+
+def test_berendsen_barostat_ideal_gas_volume_relaxes_geometrically(orc):
+    """No forces: P_n = N T / V_n with T fixed, and mu^d = 1 - c (P_t - P_n),
+    c = beta n_baro dt / tau_P, so V_{n+1} - V* = (1 - c P_t)(V_n - V*) with
+    V* = N T / P_t."""
+    x, v, sigma, L = _ideal_gas(d=3, N=400, seed=7)
+    N, d = x.shape
+    T = 2 * orc.kinetic(v) / (d * (N - 1))
+    Pt, tau_P, beta, nb, dt = 2.5, 0.5, 0.3, 10, 0.004
+    c = beta * nb * dt / tau_P
+    Vs = N * T * (N - 1) / N / Pt          # P = 2K/(dV) = (N - 1) T / V
+    V0 = L ** d
+    for cycles in (1, 3, 8):
+        r = orc.md_npt(x, v, sigma, L, cycles * nb, dt, Pt, tau_P, beta, nb, skin=2.0)
+        assert r["rescales"] == cycles
+        assert r["L"] ** d - Vs == pytest.approx((1 - c * Pt) ** cycles * (V0 - Vs), rel=1e-9)
