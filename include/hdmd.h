@@ -183,6 +183,23 @@ hdmd_status compute_forces(hdmd_system *sys, double *energy, double *virial);
  * lists and runs again. */
 hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last);
 
+/* Berendsen barostat (Berendsen et al. 1984; the NPT control of Sec. II.E).
+ * With tau_P > 0, md_steps runs in pieces of n_baro steps; after each full
+ * piece (counted across calls) the pressure P = (2K + W)/(d L^d) of its end
+ * state gives mu = [1 - beta (n_baro dt / tau_P)(P_target - P)]^(1/d), every
+ * position and the box side are multiplied by mu (box centred at the
+ * origin), the subcell grid of Eq. (7) is set up again for the new box and
+ * the lists are rebuilt (as the paper's Berendsen() does when n_cell
+ * changes).  beta: compressibility (> 0); n_baro >= 1.  tau_P <= 0 turns it
+ * off.  md_steps fails with HDMD_E_INVALID if a rescaling would leave the
+ * box below twice the largest diameter; hdmd_info.n_cell and get_box report
+ * the current box. */
+hdmd_status set_barostat(hdmd_system *sys, double P_target, double tau_P, double beta,
+                         int64_t n_baro);
+
+/* Current box side (it changes under the barostat). */
+hdmd_status get_box(hdmd_system *sys, double *L);
+
 /* Observables of Sec. II.E against a reference configuration (the paper's
  * r_i(0), taken at step n_msdstart):
  *   msd = <|dr|^2>, mqd = <|dr|^4> over the N atoms, dr = unwrapped

@@ -1,4 +1,5 @@
-// kernels_obs.cu -- on-device observables of Sec. II.E: mean squared and
+// kernels_obs.cu -- the Berendsen barostat's rescaling of the positions and
+// the on-device observables of Sec. II.E: mean squared and
 // quartic displacements since a reference configuration, the non-Gaussian
 // parameter alpha_2 (Eq. (14)), the overlap function f_ov (Eq. (15)), the
 // self part of the van Hove function G_s(r, t) (Eq. (16)) as a histogram,
@@ -74,6 +75,25 @@ __global__ void __launch_bounds__(NT) k_observe(Dev dv, const double *ref, doubl
     block_reduce_and_fold<NT>(dv, acc, R_P + 1, dv.maxblocks, sh);
 }
 
+// Berendsen barostat: every position (x0 + dlt, the box centred at the
+// origin) is multiplied by mu; the displacement since the build is folded
+// into x0 (the list build that follows wraps and rebins)
+template <int D>
+__global__ void k_scale_positions(Dev dv, double mu) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= dv.N) return;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const size_t o = (size_t)k * dv.Npad + s;
+        dv.x0[o] = mu * (dv.x0[o] + dv.dlt[o]);
+        dv.dlt[o] = 0.0;
+    }
+}
+
+template <int D> void scale_impl(const Dev &dv, double mu, cudaStream_t s) {
+    k_scale_positions<D><<<nblk(dv.N), NT, 0, s>>>(dv, mu);
+}
+
 template <int D> void ref_impl(const Dev &dv, double *ref, cudaStream_t s) {
     k_ref_from_current<D><<<nblk(dv.N), NT, 0, s>>>(dv, ref);
 }
@@ -84,6 +104,9 @@ template <int D> void observe_impl(const Dev &dv, const double *ref, double a2, 
 
 }  // namespace
 
+void launch_scale_positions(const Dev &dv, double mu, cudaStream_t s) {
+    HDMD_DISPATCH_D(dv.d, scale_impl, dv, mu, s);
+}
 void launch_reference(const Dev &dv, double *ref, cudaStream_t s) {
     HDMD_DISPATCH_D(dv.d, ref_impl, dv, ref, s);
 }

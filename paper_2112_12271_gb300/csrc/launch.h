@@ -34,6 +34,8 @@ void launch_export(const Dev &dv, double *x_rm, int32_t *img_rm, double *v_rm, d
 // caller order; displacement sums into dv.red[0..2], Z count into
 // dv.red[R_P], G_s counts into hist
 void launch_reference(const Dev &dv, double *ref, cudaStream_t s);
+// Berendsen barostat: x <- mu x for every atom (kernels_obs.cu)
+void launch_scale_positions(const Dev &dv, double mu, cudaStream_t s);
 void launch_observe(const Dev &dv, const double *ref, double a2, int nbins, double inv_w,
                     unsigned int *hist, int want_z, cudaStream_t s);
 // the whole list build: wrap + bin + counting sort + reorder + Verlet lists.

@@ -121,6 +121,9 @@ struct hdmd_system {
     std::string graph_err;
     double sigma_max = 0;
     double nvt_T = 0.0, nvt_tau = 0.0;   // Berendsen thermostat (tau <= 0: NVE)
+    double baro_P = 0.0, baro_tau = 0.0, baro_beta = 0.0;   // Berendsen barostat
+    int64_t baro_n = 0, baro_count = 0;
+    int64_t cell_cap = 0;              // subcells the cell arrays hold
     double *obs_ref = nullptr;         // reference positions [N][d], caller order
     unsigned int *obs_hist = nullptr;  // G_s counts
     int obs_hist_cap = 0;
@@ -1069,6 +1072,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     DA2(dv.gs0, Np * RF); DA2(dv.gs[0], Np * RF); DA2(dv.gs[1], Np * RF);
     DA2(dv.gd[0], Np * RD); DA2(dv.gd[1], Np * RD);
     DA2(dv.cell_count, dv.ncells); DA2(dv.cell_fill, dv.ncells); DA2(dv.cell_start, dv.ncells + 1);
+    sys->cell_cap = dv.ncells;
     DA2(dv.cell_of, Np); DA2(dv.perm, Np); DA2(dv.cellid, Np); DA2(dv.batch_start, dv.ncells + 1);
     DA2(dv.tx, nd); DA2(dv.tv, nd); DA2(dv.tsig, Np); DA2(dv.tim, Np);
     DA2(dv.timg, nd); DA2(dv.tid, Np);
@@ -1292,12 +1296,13 @@ hdmd_status compute_forces(hdmd_system *sys, double *energy, double *virial) {
     return check_device_errors(sys);
 }
 
-hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
-    hdmd_status st = validate_sys(sys);
-    if (st) return st;
-    if (nsteps < 0) return fail(sys, HDMD_E_INVALID, "nsteps must be >= 0");
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(sys, HDMD_E_INVALID, "dt must be positive");
-    st = snapshot(sys, false);
+}  // extern "C"
+
+namespace {
+
+// nsteps in the current box, restarting from a snapshot on list overflow
+hdmd_status md_fixed_box(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
+    hdmd_status st = snapshot(sys, false);
     if (st) return st;
     const int buf0 = sys->buf;
     for (int attempt = 0; attempt < 4; ++attempt) {
@@ -1312,6 +1317,115 @@ hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *l
         if (st) return st;
     }
     return fail(sys, HDMD_E_NBR_OVERFLOW, "Verlet list kept overflowing during md_steps");
+}
+
+// Berendsen barostat step: positions and box side times mu, subcell grid
+// recomputed (cell arrays grown when the grid grows), lists rebuilt
+hdmd_status rescale_box(hdmd_system *sys, double mu) {
+    Dev &dv = sys->dv;
+    const double L = sys->L * mu;
+    if (!(L > 2.0 * sys->sigma_max) || !std::isfinite(L))
+        return fail(sys, HDMD_E_INVALID, "barostat: the box would fall below twice the largest diameter");
+    int n = std::max(1, (int)std::floor(L / (sys->sigma_max + sys->pot.skin)));   // Eq. (7)
+    while (n > 2 && std::pow((double)n, sys->d) > 8.0 * (double)sys->N + 4096.0) --n;
+    int64_t nc = 1;
+    for (int k = 0; k < sys->d; ++k) nc *= n;
+    if (nc > sys->cell_cap) {
+        int32_t **arrs[4] = {&dv.cell_count, &dv.cell_fill, &dv.cell_start, &dv.batch_start};
+        for (auto pp : arrs) {
+            void *q = nullptr;
+            if (pool_alloc(&q, sizeof(int32_t) * (size_t)(nc + 1), sys->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(sys, HDMD_E_NOMEM, "barostat: subcell arrays");
+            }
+            auto it = std::find(sys->allocs.begin(), sys->allocs.end(), (void *)*pp);
+            if (it != sys->allocs.end()) *it = q;
+            else sys->allocs.push_back(q);
+            pool_free(*pp, sys->stream);
+            *pp = (int32_t *)q;
+        }
+        CK(cudaMemsetAsync(dv.cell_count, 0, sizeof(int32_t) * (size_t)nc, sys->stream));
+        sys->cell_cap = nc;
+    }
+    launch_scale_positions(dv, mu, sys->stream);
+    CKL(sys);
+    sys->L = L;
+    dv.L = L;
+    dv.halfL = 0.5 * L;
+    dv.invL = 1.0 / L;
+    dv.n = n;
+    dv.ncells = (int)nc;
+    dv.Lsc = L / n;
+    dv.invLsc = n / L;
+    dv.Lsc_f = (float)dv.Lsc;
+    dv.L_f = (float)L;
+    dv.halfL_f = (float)(0.5 * L);
+    free_graphs(sys);          // the graphs hold the box in their kernel arguments
+    sys->F_valid = false;
+    sys->rows32_valid = sys->rows64_valid = false;
+    return build_forced(sys, sys->buf);
+}
+
+}  // namespace
+
+extern "C" {
+
+hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (nsteps < 0) return fail(sys, HDMD_E_INVALID, "nsteps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(sys, HDMD_E_INVALID, "dt must be positive");
+    if (!(sys->baro_tau > 0.0)) return md_fixed_box(sys, nsteps, dt, last);
+    hdmd_thermo th{};
+    int64_t left = nsteps, done = 0, rebuilds = 0;
+    bool rescaled_last = false;
+    while (left > 0) {
+        const int64_t chunk = std::min(left, sys->baro_n - sys->baro_count);
+        st = md_fixed_box(sys, chunk, dt, &th);
+        if (st) return st;
+        rebuilds += th.rebuilds;
+        left -= chunk;
+        done += chunk;
+        sys->baro_count += chunk;
+        rescaled_last = false;
+        if (sys->baro_count == sys->baro_n) {
+            const double base = 1.0 - sys->baro_beta * ((double)sys->baro_n * dt / sys->baro_tau) *
+                                          (sys->baro_P - th.P);
+            if (!(base > 0.0))
+                return fail(sys, HDMD_E_INVALID, "barostat: the rescaling would make the box vanish");
+            st = rescale_box(sys, std::pow(base, 1.0 / sys->d));
+            if (st) return st;
+            sys->baro_count = 0;
+            rescaled_last = true;
+            ++rebuilds;
+        }
+    }
+    if (rescaled_last || nsteps == 0) {   // thermo of the (rescaled) end state
+        st = md_fixed_box(sys, 0, dt, &th);
+        if (st) return st;
+    }
+    if (last) {
+        *last = th;
+        last->steps = done;
+        last->rebuilds = rebuilds;
+    }
+    return HDMD_OK;
+}
+
+hdmd_status set_barostat(hdmd_system *sys, double P_target, double tau_P, double beta,
+                         int64_t n_baro) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (!std::isfinite(P_target) || std::isnan(tau_P))
+        return fail(sys, HDMD_E_INVALID, "P_target must be finite");
+    if (tau_P > 0.0 && (!(beta > 0.0) || !std::isfinite(beta) || n_baro < 1))
+        return fail(sys, HDMD_E_INVALID, "barostat needs beta > 0 and n_baro >= 1");
+    sys->baro_P = P_target;
+    sys->baro_tau = tau_P > 0.0 && std::isfinite(tau_P) ? tau_P : 0.0;
+    sys->baro_beta = beta;
+    sys->baro_n = n_baro;
+    sys->baro_count = 0;
+    return HDMD_OK;
 }
 
 hdmd_status fire_minimize(hdmd_system *sys, const hdmd_fire_params *params, hdmd_fire_result *res) {
@@ -1522,6 +1636,13 @@ hdmd_status observables(hdmd_system *sys, double a_ov, int nbins, double r_max,
     out->Z = sys->h_red[R_P] / N;
     if (gs)
         for (int b = 0; b < nbins; ++b) gs[b] = (double)h[b] / (N * w);
+    return HDMD_OK;
+}
+
+hdmd_status get_box(hdmd_system *sys, double *L) {
+    if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
+    if (!L) return fail(sys, HDMD_E_INVALID, "L is NULL");
+    *L = sys->L;
     return HDMD_OK;
 }
 

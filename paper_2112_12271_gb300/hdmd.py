@@ -115,6 +115,8 @@ def lib():
             "md_steps": [vp, i64, dbl, vp],
             "set_thermostat": [vp, dbl, dbl],
             "set_reference": [vp, vp],
+            "set_barostat": [vp, dbl, dbl, dbl, i64],
+            "get_box": [vp, C.POINTER(dbl)],
             "observables": [vp, dbl, i32, dbl, vp, vp],
             "fire_minimize": [vp, vp, vp],
             "swap_sweep": [vp, i32, dbl, dbl, C.c_uint64, vp, vp, i64, C.POINTER(i64), vp],
@@ -271,6 +273,17 @@ def observables(h, a_ov=0.0, nbins=0, r_max=0.0):
     return out
 
 
+def set_barostat(h, P_target, tau_P, beta=1.0, n_baro=10):
+    """Berendsen NPT for later md_steps (tau_P <= 0: fixed box)."""
+    _check(lib().set_barostat(h, float(P_target), float(tau_P), float(beta), int(n_baro)), h)
+
+
+def get_box(h):
+    L = C.c_double()
+    _check(lib().get_box(h, C.byref(L)), h)
+    return L.value
+
+
 def set_thermostat(h, T_target, tau):
     """Berendsen NVT for later md_steps (tau <= 0: back to NVE)."""
     _check(lib().set_thermostat(h, float(T_target), float(tau)), h)
@@ -363,6 +376,12 @@ class System:
 
     def thermostat(self, T_target, tau):
         set_thermostat(self.h, T_target, tau)
+
+    def barostat(self, P_target, tau_P, beta=1.0, n_baro=10):
+        set_barostat(self.h, P_target, tau_P, beta, n_baro)
+
+    def box(self):
+        return get_box(self.h)
 
     def set_reference(self, x_ref=None):
         set_reference(self.h, x_ref)
