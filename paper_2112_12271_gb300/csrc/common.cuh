@@ -111,7 +111,12 @@ struct Dev {
 };
 
 // home atoms held in registers by one warp of the list build
-__host__ __device__ constexpr int home_batch(int d) { return d <= 7 ? 8 : 4; }
+// (4 for every d: measured against 2, 3, 6 and 8, it leaves registers for
+// six resident blocks per SM, which hides the latency of the row loads)
+#ifndef HDMD_HOME_BATCH_LO
+#define HDMD_HOME_BATCH_LO 4
+#endif
+__host__ __device__ constexpr int home_batch(int d) { return d <= 7 ? HDMD_HOME_BATCH_LO : 4; }
 
 template <int D> struct Rows {
     static constexpr int RF = (D + 1 + 3) & ~3;   // floats per FP32 row

@@ -36,7 +36,7 @@ constexpr int NT = 128;   // threads per block: 4 warps, one home batch each
 
 template <int D, bool WRAP>
 #ifndef HDMD_NBR_MIN_BLOCKS
-#define HDMD_NBR_MIN_BLOCKS 4
+#define HDMD_NBR_MIN_BLOCKS 6
 #endif
 __global__ void __launch_bounds__(NT, HDMD_NBR_MIN_BLOCKS) k_nbr_build(Dev dv, bool guarded) {
     if (guarded && *((volatile int *)&dv.flags->rebuild) == 0) return;
