@@ -111,15 +111,33 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
         constexpr int U = HDMD_FORCE_UNROLL;   // list entries in flight per lane
         const int64_t lstride = (int64_t)Np << lgG;
         int64_t pos0 = ((int64_t)i << lgG) + g;
+        // the list entries of the next chunk are loaded one chunk ahead (the
+        // first chunk before the list length is known: any slot below the
+        // capacity may be read; the length decides which entries count)
+        int jn[U];
+        uint32_t cn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = g + u * G < dv.cap;
+            jn[u] = in ? dv.nbr[pos0 + u * lstride] : -1;
+            cn[u] = in ? dv.code[pos0 + u * lstride] : 0u;
+        }
         for (int m0 = g; m0 < nn; m0 += U * G, pos0 += U * lstride) {
             int jv[U];
             uint32_t cv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const bool ok = m0 + u * G < nn;
-                const int64_t pos = pos0 + u * lstride;
-                jv[u] = ok ? dv.nbr[pos] : -1;
-                cv[u] = ok ? dv.code[pos] : 0u;
+                jv[u] = m0 + u * G < nn ? jn[u] : -1;
+                cv[u] = cn[u];
+            }
+            if (m0 + U * G < nn) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = m0 + (U + u) * G < nn;
+                    const int64_t pos = pos0 + (U + u) * lstride;
+                    jn[u] = ok ? dv.nbr[pos] : -1;
+                    cn[u] = ok ? dv.code[pos] : 0u;
+                }
             }
             float rj[U][RF];
 #pragma unroll

@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
     __shared__ int sBad;
     if (cfg.fire_red && dv.flags->fire[FS_STATUS] != (double)FIRE_RUNNING) return;  // loop ended
     const int G = dv.G, lgG = dv.lgG, APB = NT >> lgG;
+    const int lgAPB = __ffs(NT) - 1 - lgG;   // APB is a power of two
     const int al = threadIdx.x >> lgG, g = threadIdx.x & (G - 1);
     const int base = blockIdx.x * APB;
     const int i = base + al;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
     const double lam = nvt ? dv.flags->nvt_lambda : 1.0;
     double kin = 0.0;
     for (int t = threadIdx.x; t < APB * D; t += NT) {
-        const int k = t / APB, a = t - k * APB, ii = base + a;
+        const int k = t >> lgAPB, a = t & (APB - 1), ii = base + a;
         if (ii >= dv.N) continue;
         const size_t o = (size_t)k * Np + ii;
         const double F = cfg.compute_force ? (double)sF[a * D + k] : dv.F[o];
