@@ -89,11 +89,19 @@ typedef struct {
  * the iteration runs with FP32 pair forces until max_i |F_i| < polish_tol
  * times the law's stiffness factor (1 harmonic, 2 (a max sigma)^2 Morse), or
  * until n_neg_max P <= 0 steps in a row show that FP32 rounding stalls it,
- * then continues with FP64 pair forces (0 disables the switch). */
+ * then continues with FP64 pair forces (0 disables the switch).
+ * The paper's own criteria and cap (Sec. II.B, Table II; each off when 0):
+ * e_thres stops when the average pair energy E_pair/N < e_thres (the
+ * paper's pushoff uses e_thres = eps); f_thres stops when the fractional
+ * drop |(E_{i+1} - E_i)/E_i| (Eq. (6)) stays below it for ten consecutive
+ * iterations; dx_max > 0 caps each atom's move per iteration (the step
+ * dt v_i and the back-off (dt/2) v_i) at length dx_max (system path only;
+ * the batched engine rejects it). */
 typedef struct {
     double dt0, dt_max, dt_min, f_inc, f_dec, alpha0, f_alpha, f_tol, polish_tol;
     int64_t n_delay, n_neg_max, max_iter;
     int initial_delay;
+    double e_thres, f_thres, dx_max;
 } hdmd_fire_params;
 
 typedef struct {

@@ -346,7 +346,7 @@ def md_npt(x, v, sigma, L, nsteps, dt, P_target, tau_P, beta, n_baro, skin=0.3, 
 
 FIRE_DEFAULTS = dict(dt0=0.005, dt_max=0.05, dt_min=1e-4, f_inc=1.1, f_dec=0.5,
                      alpha0=0.25, f_alpha=0.99, f_tol=1e-10, n_delay=20, n_neg_max=2000,
-                     max_iter=1000000, initial_delay=1)
+                     max_iter=1000000, initial_delay=1, e_thres=0.0, f_thres=0.0, dx_max=0.0)
 
 
 class _FireParams(C.Structure):
@@ -354,7 +354,8 @@ class _FireParams(C.Structure):
                 ("f_inc", C.c_double), ("f_dec", C.c_double), ("alpha0", C.c_double),
                 ("f_alpha", C.c_double), ("f_tol", C.c_double), ("n_delay", C.c_int64),
                 ("n_neg_max", C.c_int64), ("max_iter", C.c_int64),
-                ("initial_delay", C.c_int)]
+                ("initial_delay", C.c_int), ("e_thres", C.c_double), ("f_thres", C.c_double),
+                ("dx_max", C.c_double)]
 
 
 def fire(x, sigma, L, skin=0.3, eps=1.0, mass=None, **params):

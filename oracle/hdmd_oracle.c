@@ -583,6 +583,7 @@ typedef struct {
     double dt0, dt_max, dt_min, f_inc, f_dec, alpha0, f_alpha, f_tol;
     int64_t n_delay, n_neg_max, max_iter;
     int initial_delay;
+    double e_thres, f_thres, dx_max;   /* the paper's options; 0 = off */
 } orc_fire_params;
 
 /* FIRE 2.0 energy minimisation with the semi-implicit Euler integrator
@@ -599,6 +600,12 @@ typedef struct {
  *     x -= (dt/2) v and v = 0;
  *   - v += dt F/m; if P > 0, v = (1-alpha) v + alpha |v| F/|F| with norms
  *     over all atoms; x += dt v; F = F(x).
+ * The paper's own stop criteria (Sec. II.B), each off when 0: the average
+ * pair energy E_pair/N below e_thres; or the fractional energy drop
+ * |(E_{i+1} - E_i)/E_i| (Eq. (6)) below f_thres for ten consecutive
+ * iterations.  dx_max > 0 (Table II's maximum displacement per time step):
+ * an atom whose move (the step dt v_i, or the back-off (dt/2) v_i) is
+ * longer than dx_max moves dx_max along it instead.
  * v is zeroed on entry.  out[0..3] = iterations, final E_pair, final
  * max_i |F_i|, builds.  Returns 0 on convergence, 1 if max_iter was hit,
  * 2 if the P <= 0 count ran out. */
@@ -613,6 +620,8 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
     memset(v, 0, sizeof(double) * (size_t)(N * d));
     vl_build(&vl, d, N, L, x, sigma, skin);
     orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
+    double E_prev = 0.0;
+    int64_t nflat = 0;
     for (;;) {
         double fmax2 = 0.0;
         for (int64_t i = 0; i < N; ++i) {
@@ -620,7 +629,14 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
             for (int k = 0; k < d; ++k) s += F[i * d + k] * F[i * d + k];
             if (s > fmax2) fmax2 = s;
         }
+        if (p->f_thres > 0.0) {
+            if (it > 0 && E_prev != 0.0 && fabs((E - E_prev) / E_prev) < p->f_thres) nflat++;
+            else nflat = 0;
+            E_prev = E;
+        }
         if (sqrt(fmax2) < p->f_tol) { status = 0; break; }
+        if (p->e_thres > 0.0 && E / (double)N < p->e_thres) { status = 0; break; }
+        if (p->f_thres > 0.0 && nflat >= 10) { status = 0; break; }
         if (it >= p->max_iter) { status = 1; break; }
 
         double P = 0.0;
@@ -640,9 +656,17 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
                 dt = fmax(dt * p->f_dec, p->dt_min);
                 alpha = p->alpha0;
             }
-            for (int64_t a = 0; a < N * d; ++a) {
-                x[a] -= 0.5 * dt * v[a];
-                v[a] = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double c = 1.0;
+                if (p->dx_max > 0.0) {
+                    double st2 = 0.0;
+                    for (int k = 0; k < d; ++k) st2 += (0.5 * dt * v[i * d + k]) * (0.5 * dt * v[i * d + k]);
+                    if (st2 > p->dx_max * p->dx_max) c = p->dx_max / sqrt(st2);
+                }
+                for (int k = 0; k < d; ++k) {
+                    x[i * d + k] -= c * (0.5 * dt * v[i * d + k]);
+                    v[i * d + k] = 0.0;
+                }
             }
         }
         for (int64_t i = 0; i < N; ++i) {
@@ -657,11 +681,18 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
                 for (int64_t a = 0; a < N * d; ++a)
                     v[a] = (1.0 - alpha) * v[a] + alpha * vn * F[a] / fn;
         }
-        for (int64_t i = 0; i < N; ++i)
+        for (int64_t i = 0; i < N; ++i) {
+            double c = 1.0;
+            if (p->dx_max > 0.0) {
+                double st2 = 0.0;
+                for (int k = 0; k < d; ++k) st2 += (dt * v[i * d + k]) * (dt * v[i * d + k]);
+                if (st2 > p->dx_max * p->dx_max) c = p->dx_max / sqrt(st2);
+            }
             for (int k = 0; k < d; ++k) {
-                x[i * d + k] += dt * v[i * d + k];
+                x[i * d + k] += c * (dt * v[i * d + k]);
                 x[i * d + k] = wrap(x[i * d + k], L, img ? &img[i * d + k] : NULL);
             }
+        }
         if (vl_needs_rebuild(&vl, d, N, L, x, skin)) vl_build(&vl, d, N, L, x, sigma, skin);
         orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
         it++;

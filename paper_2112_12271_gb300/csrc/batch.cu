@@ -257,6 +257,8 @@ hdmd_status batch_add(hdmd_batch *b, const hdmd_job_spec *spec, const double *di
             return bfail(b, HDMD_E_INVALID, "non-finite position or velocity");
     if (!(spec->L > 2.0 * smax))
         return bfail(b, HDMD_E_INVALID, "box too small: L must exceed twice the largest diameter");
+    if (spec->kind != 0 && spec->fire.dt0 > 0 && spec->fire.dx_max != 0.0)
+        return bfail(b, HDMD_E_INVALID, "dx_max is not available in the batched engine");
     int n = std::max(1, (int)std::floor(spec->L / (smax + spec->skin)));   // Eq. (7)
     while (n > 2 && std::pow((double)n, d) > 8.0 * (double)N + 4096.0) --n;
     int id = -1;
@@ -345,6 +347,7 @@ hdmd_status batch_add(hdmd_batch *b, const hdmd_job_spec *spec, const double *di
     if (J.kind == JOB_FIRE) {
         hdmd_fire_params p = spec->fire;
         if (!(p.dt0 > 0)) {
+            p.e_thres = 0.0; p.f_thres = 0.0; p.dx_max = 0.0;
             p.dt0 = 0.005; p.dt_max = 0.05; p.dt_min = 1e-4; p.f_inc = 1.1; p.f_dec = 0.5;
             p.alpha0 = 0.25; p.f_alpha = 0.99; p.f_tol = 1e-10; p.polish_tol = 1e-6;
             p.n_delay = 20; p.n_neg_max = 2000; p.max_iter = 1000000; p.initial_delay = 1;
@@ -365,6 +368,11 @@ hdmd_status batch_add(hdmd_batch *b, const hdmd_job_spec *spec, const double *di
         fs[FP_NNEGMAX] = (double)p.n_neg_max;
         fs[FP_MAXITER] = (double)p.max_iter;
         fs[FP_INITDELAY] = p.initial_delay ? 1.0 : 0.0;
+        fs[FP_ETHRES] = p.e_thres;
+        fs[FP_FTHRES] = p.f_thres;
+        fs[FP_DXMAX] = 0.0;
+        fs[FP_NATOMS] = (double)N;
+        fs[FS_FITER] = -1.0;
     }
     if ((e = cudaMemcpyAsync(b->d_jobs + id, &J, sizeof(J), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail_free("descriptor", e);

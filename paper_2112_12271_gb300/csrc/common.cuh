@@ -53,9 +53,11 @@ __host__ __device__ constexpr bool red_is_max(int r) { return r == R_DMAX2 || r 
 enum FireSlot {
     FS_DT = 0, FS_ALPHA, FS_NPOS, FS_NNEG, FS_ITER, FS_BRANCH, FS_VNORM, FS_FNORM,
     FS_STATUS, FS_FMAX, FS_E, FS_PHASE_ITER,
+    FS_EPREV, FS_NFLAT, FS_FITER,   // the fractional-drop criterion
     // parameters
     FP_DTMAX, FP_DTMIN, FP_FINC, FP_FDEC, FP_ALPHA0, FP_FALPHA, FP_FTOL, FP_SWITCH,
     FP_NDELAY, FP_NNEGMAX, FP_MAXITER, FP_INITDELAY,
+    FP_ETHRES, FP_FTHRES, FP_DXMAX, FP_NATOMS,
     FS_COUNT
 };
 enum FireStatus { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_NEGFAIL = 3,

@@ -3,7 +3,9 @@
 // thread after the force reduction of an iteration.  fs holds the state and
 // parameters (FireSlot indices), red the reduced sums (Red indices) of the
 // forces and velocities at the current positions.  Order of tests: converged
-// (max_i |F_i| < f_tol), precision switch, max_iter; then the P = F.v rules.
+// (max_i |F_i| < f_tol; or the paper's criteria of Sec. II.B when set:
+// E_pair/N < e_thres, or the fractional drop below f_thres ten iterations
+// in a row), precision switch, max_iter; then the P = F.v rules.
 // The precision switch (FP32 -> FP64 pair forces) happens below the switch
 // threshold, or when the FP32 phase stalls (n_neg_max P <= 0 steps in a row).
 // Writes and returns the new status.
@@ -15,10 +17,22 @@ namespace hdmd {
 __device__ __forceinline__ int fire_scalar_update(double *fs, const double *red) {
     const double fmx = sqrt(red[R_FMAX2]);
     fs[FS_FMAX] = fmx;
-    fs[FS_E] = 0.5 * red[R_E];
+    const double E = 0.5 * red[R_E];
+    fs[FS_E] = E;
+    // the paper's fractional drop |(E_{i+1} - E_i)/E_i| (Eq. (6)), counted
+    // once per iteration (a precision switch re-evaluates the same one)
+    if (fs[FP_FTHRES] > 0.0 && fs[FS_ITER] != fs[FS_FITER]) {
+        const double Ep = fs[FS_EPREV];
+        const bool flat = fs[FS_ITER] > 0.0 && Ep != 0.0 && fabs((E - Ep) / Ep) < fs[FP_FTHRES];
+        fs[FS_NFLAT] = flat ? fs[FS_NFLAT] + 1.0 : 0.0;
+        fs[FS_EPREV] = E;
+        fs[FS_FITER] = fs[FS_ITER];
+    }
     int status = FIRE_RUNNING;
     if (red[R_BAD] != 0.0) status = FIRE_NEGFAIL;
     else if (fmx < fs[FP_FTOL]) status = FIRE_CONVERGED;
+    else if (fs[FP_ETHRES] > 0.0 && E / fs[FP_NATOMS] < fs[FP_ETHRES]) status = FIRE_CONVERGED;
+    else if (fs[FP_FTHRES] > 0.0 && fs[FS_NFLAT] >= 10.0) status = FIRE_CONVERGED;
     else if (fmx < fs[FP_SWITCH]) status = FIRE_SWITCH;
     else if (fs[FS_ITER] >= fs[FP_MAXITER]) status = FIRE_MAXITER;
     else {

@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
     constexpr int APB = NT / 4;
     __shared__ float sPos[APB * RF];
     __shared__ float sD2[APB];
+    __shared__ double sBack[APB * D], sStep[APB * D], sCB[APB], sCS[APB];
     const double *fs = dv.flags->fire;
     if (fs[FS_STATUS] != (double)FIRE_RUNNING) return;
     const double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
@@ -271,25 +272,62 @@ __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
     const double vn = fs[FS_VNORM], fn = fs[FS_FNORM];
     const bool mix = up && fn > 0.0;
     const double cf = mix ? alpha * vn / fn : 0.0;
+    const double dxm = fs[FP_DXMAX];
     const int base = blockIdx.x * APB;
     const int Np = dv.Npad;
     for (int a = threadIdx.x; a < APB; a += NT) sD2[a] = 0.f;
     __syncthreads();
+    if (dxm > 0.0) {
+        // Table II's displacement cap: an atom whose back-off (dt/2) v or
+        // step dt v is longer than dx_max moves dx_max along it; the
+        // per-atom lengths are summed over the axes in order (repeatable)
+        for (int t = threadIdx.x; t < APB * D; t += NT) {
+            const int k = t / APB, a = t - k * APB, ii = base + a;
+            if (ii >= dv.N) continue;
+            const size_t o = (size_t)k * Np + ii;
+            const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
+            double v = dv.v[o];
+            const double F = dv.F[o];
+            sBack[a * D + k] = up ? 0.0 : 0.5 * dt * v;
+            if (!up) v = 0.0;
+            v += dt * F * im;
+            if (mix) v = (1.0 - alpha) * v + cf * F;
+            dv.v[o] = v;
+            sStep[a * D + k] = dt * v;
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < APB; a += NT) {
+            double b2 = 0.0, s2 = 0.0;
+            for (int k = 0; k < D; ++k) {
+                b2 += sBack[a * D + k] * sBack[a * D + k];
+                s2 += sStep[a * D + k] * sStep[a * D + k];
+            }
+            sCB[a] = b2 > dxm * dxm ? dxm / sqrt(b2) : 1.0;
+            sCS[a] = s2 > dxm * dxm ? dxm / sqrt(s2) : 1.0;
+        }
+        __syncthreads();
+    }
     for (int t = threadIdx.x; t < APB * D; t += NT) {
         const int k = t / APB, a = t - k * APB, ii = base + a;
         if (ii >= dv.N) continue;
         const size_t o = (size_t)k * Np + ii;
-        const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
-        double v = dv.v[o], dl = dv.dlt[o];
-        const double F = dv.F[o];
-        if (!up) {
-            dl -= 0.5 * dt * v;
-            v = 0.0;
+        double dl = dv.dlt[o];
+        if (dxm > 0.0) {
+            dl -= sCB[a] * sBack[a * D + k];
+            dl += sCS[a] * sStep[a * D + k];
+        } else {
+            const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
+            double v = dv.v[o];
+            const double F = dv.F[o];
+            if (!up) {
+                dl -= 0.5 * dt * v;
+                v = 0.0;
+            }
+            v += dt * F * im;
+            if (mix) v = (1.0 - alpha) * v + cf * F;
+            dl += dt * v;
+            dv.v[o] = v;
         }
-        v += dt * F * im;
-        if (mix) v = (1.0 - alpha) * v + cf * F;
-        dl += dt * v;
-        dv.v[o] = v;
         dv.dlt[o] = dl;
         const float fl = (float)dl;
         atomicAdd(&sD2[a], fl * fl);

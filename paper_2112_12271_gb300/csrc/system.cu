@@ -756,6 +756,11 @@ hdmd_status fire_once(hdmd_system *sys, const hdmd_fire_params &p, hdmd_fire_res
     fs[FP_NNEGMAX] = (double)p.n_neg_max;
     fs[FP_MAXITER] = (double)p.max_iter;
     fs[FP_INITDELAY] = p.initial_delay ? 1.0 : 0.0;
+    fs[FP_ETHRES] = p.e_thres;
+    fs[FP_FTHRES] = p.f_thres;
+    fs[FP_DXMAX] = p.dx_max;
+    fs[FP_NATOMS] = (double)sys->N;
+    fs[FS_FITER] = -1.0;
     std::memcpy(sys->h_flags->fire, fs, sizeof(fs));
     CK(cudaMemcpyAsync(dv.flags->fire, sys->h_flags->fire, sizeof(fs), cudaMemcpyHostToDevice, sys->stream));
     CK(cudaMemcpyAsync(&sys->h_flags->nbuilds, &dv.flags->nbuilds, sizeof(int), cudaMemcpyDeviceToHost, sys->stream));
@@ -1438,7 +1443,11 @@ hdmd_status fire_minimize(hdmd_system *sys, const hdmd_fire_params *params, hdmd
         p.dt0 = 0.005; p.dt_max = 0.05; p.dt_min = 1e-4; p.f_inc = 1.1; p.f_dec = 0.5;
         p.alpha0 = 0.25; p.f_alpha = 0.99; p.f_tol = 1e-10; p.polish_tol = 1e-6;
         p.n_delay = 20; p.n_neg_max = 2000; p.max_iter = 1000000; p.initial_delay = 1;
+        p.e_thres = 0.0; p.f_thres = 0.0; p.dx_max = 0.0;
     }
+    if (!(p.e_thres >= 0) || !(p.f_thres >= 0) || !(p.dx_max >= 0) || !std::isfinite(p.e_thres) ||
+        !std::isfinite(p.f_thres) || !std::isfinite(p.dx_max))
+        return fail(sys, HDMD_E_INVALID, "e_thres, f_thres and dx_max must be >= 0 and finite");
     if (!(p.dt0 > 0) || !(p.dt_max >= p.dt0) || !(p.dt_min > 0) || !(p.dt_min <= p.dt0) ||
         !(p.f_inc >= 1) || !(p.f_dec > 0 && p.f_dec <= 1) || !(p.alpha0 >= 0 && p.alpha0 <= 1) ||
         !(p.f_alpha > 0 && p.f_alpha <= 1) || !(p.f_tol >= 0) || p.max_iter < 0 || p.n_delay < 0 ||

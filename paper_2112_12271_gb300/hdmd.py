@@ -55,7 +55,8 @@ class FireParams(C.Structure):
                 ("f_inc", C.c_double), ("f_dec", C.c_double), ("alpha0", C.c_double),
                 ("f_alpha", C.c_double), ("f_tol", C.c_double), ("polish_tol", C.c_double),
                 ("n_delay", C.c_int64), ("n_neg_max", C.c_int64), ("max_iter", C.c_int64),
-                ("initial_delay", C.c_int)]
+                ("initial_delay", C.c_int), ("e_thres", C.c_double), ("f_thres", C.c_double),
+                ("dx_max", C.c_double)]
 
 
 class FireResult(C.Structure):
@@ -89,7 +90,7 @@ JOB_RUNNING, JOB_DONE, JOB_NOT_CONVERGED, JOB_ERROR = 0, 1, 2, 3
 
 FIRE_DEFAULTS = dict(dt0=0.005, dt_max=0.05, dt_min=1e-4, f_inc=1.1, f_dec=0.5, alpha0=0.25,
                      f_alpha=0.99, f_tol=1e-10, polish_tol=1e-6, n_delay=20, n_neg_max=2000,
-                     max_iter=1000000, initial_delay=1)
+                     max_iter=1000000, initial_delay=1, e_thres=0.0, f_thres=0.0, dx_max=0.0)
 
 _lib = None
 
