@@ -380,13 +380,14 @@ def run_batch(args):
     return 0
 
 # -------------------------------------------------------- the paper's own model
+PAPER_TAU_T = 0.5   # Berendsen damping time (the paper names tau_temp, no value)
 def run_paper(args):
     """The paper's benchmark protocol (Sec. III) at d = 3..6: its Morse law
     (a = 30) with volume-scaled prefactors and masses, diameters of Eq. (3)
     with R = d, phi*_d of Table III, T = 0.25, dt = 0.0016, skin 0.25.  Each
     system is pushed off as the paper does (FIRE until E_pair/N < eps, each
     move capped at 0.01), given velocities at T, then run for
-    args.paper_tau time units of MD
+    args.paper_tau time units of NVT MD (Berendsen, tau_T = 0.5)
     (625 steps each) with one SWAP pass (p = 0.1) per time unit.  Reports
     atom-steps/s per d and the device time per list entry and step."""
     import torch
@@ -399,13 +400,16 @@ def run_paper(args):
     rows, total_atom_steps, total_s = [], 0, 0.0
     for d in range(3, 7):
         s = W.paper_model(d, args.paper_n, seed=d)
-        with hdmd.System(d, s.L, s.sigma, s.x, None, s.mass, skin=0.25, precision=hdmd.HDMD_MIXED,
-                         stream=stream.cuda_stream, law="morse", a=W.MORSE_A, eps_scale=True) as g:
-            # the paper's pushoff: FIRE until the average pair energy is
-            # below eps, each move capped (Sec. II.A, Table II)
+        law = dict(skin=0.25, stream=stream.cuda_stream, law="morse", a=W.MORSE_A, eps_scale=True)
+        # the paper's pushoff: FIRE until the average pair energy is below
+        # eps, each move capped (Sec. II.A, Table II); in FP64, whose range
+        # holds the Morse forces of nearly coincident random atoms
+        with hdmd.System(d, s.L, s.sigma, s.x, None, s.mass, precision=hdmd.HDMD_FP64, **law) as g:
             push = g.fire(e_thres=1.0, dx_max=0.01, dt0=W.PAPER_DT, dt_max=10 * W.PAPER_DT,
                           dt_min=0.02 * W.PAPER_DT, max_iter=100000, n_neg_max=10 ** 9)
-            g.set_state(g.state(v=False, img=False)["x"], s.v, s.mass)
+            x0 = g.state(v=False, img=False)["x"]
+        with hdmd.System(d, s.L, s.sigma, x0, s.v, s.mass, precision=hdmd.HDMD_MIXED, **law) as g:
+            g.thermostat(W.PAPER_T, PAPER_TAU_T)             # the paper's runs are NVT
             g.md_steps(steps_per_tau, W.PAPER_DT)          # warm-up: graphs, first builds
             g.set_reference()                                # r_i(0) of the observables
             a = torch.cuda.Event(enable_timing=True)
