@@ -108,7 +108,7 @@ def _load():
             lib.orc_kinetic.argtypes = [i32, i64, vp, vp]
             lib.orc_md_steps.restype = i64
             lib.orc_md_steps.argtypes = [i32, i64, dbl, vp, vp, vp, vp, vp, dbl, dbl,
-                                         dbl, i64, vp, i32, vp, dbl, dbl]
+                                         dbl, i64, vp, i32, vp, dbl, dbl, i32, i64, vp]
             lib.orc_md_npt.restype = i64
             lib.orc_md_npt.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, dbl, dbl, dbl, i64,
                                        dbl, dbl, dbl, dbl, dbl, i64, vp, vp]
@@ -305,9 +305,11 @@ def kinetic(v, mass=None):
 
 # --------------------------------------------------------------- integrators
 def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None, F=None,
-             T_target=0.0, tau=0.0):
+             T_target=0.0, tau=0.0, rule="exact", n_bet=1, step=0):
     """Velocity Verlet on copies (NVE, or NVT with the Berendsen factor
-    when tau > 0); returns dict(x, v, img, F, E, W, K, builds)."""
+    when tau > 0), lists rebuilt by the exact rule or the paper's (checked
+    every n_bet steps, step = steps already counted); returns dict(x, v, img,
+    F, E, W, K, builds, step)."""
     x = _f64(x).copy()
     v = _f64(v).copy()
     N, d = x.shape
@@ -317,10 +319,12 @@ def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None,
     have_F = F is not None
     F = np.zeros_like(x) if F is None else _f64(F).copy()
     th = np.zeros(3)
+    stp = np.array([int(step)], dtype=np.int64)
     b = _load().orc_md_steps(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
                              dt, int(nsteps), _p(F), int(have_F), _p(th), float(T_target),
-                             float(tau))
-    return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b))
+                             float(tau), {"exact": 0, "paper": 1}[rule], int(n_bet), _p(stp))
+    return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b),
+                step=int(stp[0]))
 
 
 def md_npt(x, v, sigma, L, nsteps, dt, P_target, tau_P, beta, n_baro, skin=0.3, eps=1.0,

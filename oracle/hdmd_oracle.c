@@ -503,6 +503,26 @@ static int vl_needs_rebuild(const orc_vl *vl, int d, int64_t N, double L,
     return 4.0 * dmax2 > skin * skin;
 }
 
+/* The paper's rule (Sec. II.C): rebuild when at least 0.1 % of the atoms
+ * have moved by at least s/2, or any atom by at least s, since the build.
+ * Unlike the rule above it can miss a pair that closes from both sides. */
+static int vl_needs_rebuild_paper(const orc_vl *vl, int d, int64_t N, double L,
+                                  const double *x, double skin)
+{
+    int64_t half = 0;
+    int any = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double dx = orc_min_image(x[i * d + k] - vl->x0[i * d + k], L);
+            s += dx * dx;
+        }
+        if (s >= 0.25 * skin * skin) half++;
+        if (s >= skin * skin) any = 1;
+    }
+    return any || (double)half >= 0.001 * (double)N;
+}
+
 static void vl_free(orc_vl *vl)
 {
     free(vl->counts); free(vl->idx); free(vl->x0);
@@ -530,6 +550,9 @@ static double wrap(double x, double L, int32_t *img)
  *   paper does) lambda = sqrt(1 + (dt/tau)(T_target/T - 1)), where T is the
  *   kinetic temperature 2K/(d(N-1)) at the end of the previous step (at the
  *   start of the call for the first step), and lambda = 1 when T = 0.
+ * rule 0 rebuilds the list when 2 max|dx| > s after any drift (exact
+ * forces); rule 1 applies the paper's rule (vl_needs_rebuild_paper) after
+ * every n_bet-th step, *step_count counting the steps across calls.
  * F must hold the forces at the incoming x (have_F != 0) or is computed
  * first from the list (have_F == 0); it holds those at the outgoing x on
  * return.  thermo[0..2] = E_pair, virial W, kinetic K at the end.
@@ -537,7 +560,8 @@ static double wrap(double x, double L, int32_t *img)
 int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *img,
                      const double *sigma, const double *mass, double eps,
                      double skin, double dt, int64_t nsteps, double *F, int have_F,
-                     double *thermo, double T_target, double tau)
+                     double *thermo, double T_target, double tau, int rule, int64_t n_bet,
+                     int64_t *step_count)
 {
     orc_vl vl = {0};
     double E = 0.0, W = 0.0;
@@ -553,7 +577,13 @@ int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *
                 x[i * d + k] = wrap(x[i * d + k], L, img ? &img[i * d + k] : NULL);
             }
         }
-        if (vl_needs_rebuild(&vl, d, N, L, x, skin)) vl_build(&vl, d, N, L, x, sigma, skin);
+        if (rule == 1) {   /* the paper's rule, checked every n_bet steps */
+            *step_count += 1;
+            if (*step_count % n_bet == 0 && vl_needs_rebuild_paper(&vl, d, N, L, x, skin))
+                vl_build(&vl, d, N, L, x, sigma, skin);
+        } else if (vl_needs_rebuild(&vl, d, N, L, x, skin)) {
+            vl_build(&vl, d, N, L, x, sigma, skin);
+        }
         orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
         for (int64_t i = 0; i < N; ++i) {
             double m = mass ? mass[i] : 1.0;
@@ -733,8 +763,9 @@ int64_t orc_md_npt(int d, int64_t N, double *L, double *x, double *v, int32_t *i
     while (left > 0) {
         int64_t chunk = n_baro - *count;
         if (chunk > left) chunk = left;
+        int64_t st0 = 0;
         orc_md_steps(d, N, *L, x, v, img, sigma, mass, eps, skin, dt, chunk, F, 0, thermo,
-                     T_target, tau);
+                     T_target, tau, 0, 1, &st0);
         left -= chunk;
         *count += chunk;
         rescaled_last = 0;
@@ -751,8 +782,11 @@ int64_t orc_md_npt(int d, int64_t N, double *L, double *x, double *v, int32_t *i
             rescaled_last = 1;
         }
     }
-    if (rescaled_last) orc_md_steps(d, N, *L, x, v, img, sigma, mass, eps, skin, dt, 0, F, 0,
-                                    thermo, T_target, tau);
+    if (rescaled_last) {
+        int64_t st0 = 0;
+        orc_md_steps(d, N, *L, x, v, img, sigma, mass, eps, skin, dt, 0, F, 0, thermo, T_target,
+                     tau, 0, 1, &st0);
+    }
     free(F);
     return nresc;
 }

@@ -594,3 +594,16 @@ def test_berendsen_barostat_ideal_gas_volume_relaxes_geometrically(orc):
         r = orc.md_npt(x, v, sigma, L, cycles * nb, dt, Pt, tau_P, beta, nb, skin=2.0)
         assert r["rescales"] == cycles
         assert r["L"] ** d - Vs == pytest.approx((1 - c * Pt) ** cycles * (V0 - Vs), rel=1e-9)
+
+
+def test_paper_rebuild_rule_counts_and_misses(orc):
+    """The paper's rule (Sec. II.C) rebuilds no more often than the exact
+    one, only at multiples of n_bet, and can leave forces inexact; with the
+    exact rule the forces equal brute force."""
+    s = W.make_system(3, 600, phi=0.5, dist="poly", T=0.05, seed=4)
+    ex = orc.md_steps(s.x, s.v, s.sigma, s.L, 300, 0.005, skin=0.3)
+    pp = orc.md_steps(s.x, s.v, s.sigma, s.L, 300, 0.005, skin=0.3, rule="paper", n_bet=5)
+    assert pp["step"] == 300
+    assert 1 <= pp["builds"] <= ex["builds"]
+    Fb, _, _ = orc.forces(ex["x"], s.sigma, s.L)
+    assert np.abs(ex["F"] - Fb).max() < 1e-12 * np.abs(Fb).max()
