@@ -205,6 +205,14 @@ hdmd_status md_steps(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *l
 hdmd_status set_barostat(hdmd_system *sys, double P_target, double tau_P, double beta,
                          int64_t n_baro);
 
+/* List rebuild rule.  rule 0 (default): rebuild as soon as 2 max_i |x_i -
+ * x_i(build)| > s, checked after every drift, which keeps the forces exact.
+ * rule 1: the paper's rule (Sec. II.C), checked after every n_bet-th MD
+ * step (counted from this call on): rebuild when at least 0.1 % of the
+ * atoms have moved by s/2 or any atom by s; it can miss a pair closing from
+ * both sides, so forces may deviate from the exact ones.  FIRE keeps rule 0. */
+hdmd_status set_rebuild_rule(hdmd_system *sys, int rule, int n_bet);
+
 /* Current box side (it changes under the barostat). */
 hdmd_status get_box(hdmd_system *sys, double *L);
 

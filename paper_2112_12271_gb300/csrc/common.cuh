@@ -75,6 +75,7 @@ struct Flags {
     unsigned int disp_bits;  // max |dlt|^2 of the running step (float bits)
     int pad1;
     long long total_entries; // sum of list lengths at the last build
+    long long md_step;       // MD steps since the rebuild rule was set
     double nvt_lambda;       // Berendsen factor for the next second kick
     double nvt_T;            // kinetic temperature it was computed from
     double fire[FS_COUNT];

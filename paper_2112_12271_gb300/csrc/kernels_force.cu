@@ -55,12 +55,17 @@ __device__ __forceinline__ double block_sum_fixed(double a, double *ws) {
     return t;   // valid in thread 0
 }
 
+// With rule 1 (the paper's, Sec. II.C) the trigger is evaluated after every
+// n_bet-th MD step only and fires when at least 0.1 % of the atoms have moved
+// by s/2 (blk_half: this block's count) or any atom by s.
 __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bool blk_bad,
                                              unsigned long long cond, int nvt = 0,
                                              double kin = 0.0, double rate = 0.0,
-                                             double T_target = 0.0) {
+                                             double T_target = 0.0, int rule = 0,
+                                             int n_bet = 1, int blk_half = 0) {
     __shared__ bool last;
     __shared__ unsigned wmax[32];
+    __shared__ unsigned whalf[32];
     __shared__ double wsum[32];
     unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(blk_max_d2));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
@@ -73,6 +78,7 @@ __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bo
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, wmax[w]);
         part[blockIdx.x] = b;
         if (nvt) dv.partials[(size_t)dv.maxblocks + blockIdx.x] = kblk;
+        if (rule == 1) part[(size_t)6 * dv.maxblocks + blockIdx.x] = (unsigned)blk_half;
         __threadfence();
         const unsigned t = atomicAdd(&dv.flags->counter, 1u);
         last = (t == gridDim.x - 1);
@@ -96,13 +102,29 @@ __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bo
             dv.flags->nvt_lambda = T > 0.0 ? sqrt(fmax(0.0, 1.0 + rate * (T_target / T - 1.0))) : 1.0;
         }
     }
+    if (rule == 1) {
+        unsigned h = 0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
+            h += __ldcg(part + (size_t)6 * dv.maxblocks + k);
+        h = __reduce_add_sync(0xffffffffu, h);
+        if ((threadIdx.x & 31) == 0) whalf[threadIdx.x >> 5] = h;
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         unsigned m = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
+        unsigned half = 0;
+        if (rule == 1)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) half += whalf[w];
         const float d2 = __uint_as_float(m);
         const float s2 = (float)(dv.skin * dv.skin) * (1.0f - 1e-5f);
         const bool finite = d2 <= 3.0e38f;
-        const int trig = (4.0f * d2 > s2) || !finite;
+        int trig = (4.0f * d2 > s2) || !finite;
+        if (rule == 1) {
+            const long long st = ++dv.flags->md_step;
+            trig = !finite || (st % n_bet == 0 &&
+                               ((double)half >= 0.001 * (double)dv.N || d2 >= (float)(dv.skin * dv.skin)));
+        }
         if (!finite || 16.0 * (double)d2 > dv.L * dv.L) atomicOr(&dv.flags->error, (int)ERR_LOST);
         dv.flags->rebuild = trig;
         if (cond) cudaGraphSetConditional(cond, trig ? 1u : 0u);
@@ -238,8 +260,15 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
                 if (base + a < dv.N) dv.gd[cfg.out_buf][(size_t)(base + a) * RD + D] = 0.5 * dv.sigma[base + a];
         }
         float m = 0.f;
-        for (int a = threadIdx.x; a < APB; a += NT) m = fmaxf(m, sD2[a]);
-        trigger_fold(dv, m, false, cfg.cond_rebuild, nvt ? 1 : 0, kin, cfg.nvt_rate, cfg.nvt_T);
+        int half = 0;
+        const float q2 = (float)(0.25 * dv.skin * dv.skin);
+        for (int a = threadIdx.x; a < APB; a += NT) {
+            m = fmaxf(m, sD2[a]);
+            half += base + a < dv.N && sD2[a] >= q2;
+        }
+        const int blk_half = cfg.rule == 1 ? __syncthreads_count(half) : 0;   // APB <= NT
+        trigger_fold(dv, m, false, cfg.cond_rebuild, nvt ? 1 : 0, kin, cfg.nvt_rate, cfg.nvt_T,
+                     cfg.rule, cfg.n_bet, blk_half);
     }
     if (cfg.thermo || cfg.fire_red) {
         const bool last = block_reduce_and_fold<NT>(dv, acc, R_BAD + 1, dv.maxblocks, sh);

@@ -60,6 +60,8 @@ struct StepCfg {
     int fire_red;        // reduce P, v.v, v.F/m, F.F/m^2, F.F, max|F_i|^2 and run
                          // the FIRE scalar update in the last block
     double dt, halfdt;
+    int rule;            // list rebuild rule: 0 exact (2 max|dx| > s), 1 the paper's
+    int n_bet;           // the paper's rule is checked every n_bet steps
     int nvt;             // Berendsen NVT: second kick scaled by flags->nvt_lambda
     double nvt_rate;     // dt / tau
     double nvt_T;        // target temperature

@@ -121,6 +121,7 @@ struct hdmd_system {
     std::string graph_err;
     double sigma_max = 0;
     double nvt_T = 0.0, nvt_tau = 0.0;   // Berendsen thermostat (tau <= 0: NVE)
+    int rule = 0, n_bet = 1;             // list rebuild rule (0 exact, 1 the paper's)
     double baro_P = 0.0, baro_tau = 0.0, baro_beta = 0.0;   // Berendsen barostat
     int64_t baro_n = 0, baro_count = 0;
     int64_t cell_cap = 0;              // subcells the cell arrays hold
@@ -376,6 +377,8 @@ StepCfg base_cfg(const hdmd_system *sys, double dt) {
     c.dt = dt;
     c.halfdt = 0.5 * dt;
     c.fp64_pairs = sys->prec == HDMD_FP64 ? 1 : 0;
+    c.rule = sys->rule;
+    c.n_bet = sys->n_bet;
     if (sys->nvt_tau > 0.0 && dt > 0.0) {
         c.nvt = 1;
         c.nvt_rate = dt / sys->nvt_tau;
@@ -1645,6 +1648,19 @@ hdmd_status observables(hdmd_system *sys, double a_ov, int nbins, double r_max,
     out->Z = sys->h_red[R_P] / N;
     if (gs)
         for (int b = 0; b < nbins; ++b) gs[b] = (double)h[b] / (N * w);
+    return HDMD_OK;
+}
+
+hdmd_status set_rebuild_rule(hdmd_system *sys, int rule, int n_bet) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if ((rule != 0 && rule != 1) || n_bet < 1)
+        return fail(sys, HDMD_E_INVALID, "rule must be 0 or 1 and n_bet >= 1");
+    sys->rule = rule;
+    sys->n_bet = rule == 1 ? n_bet : 1;
+    st = clear_flag_field(sys, offsetof(Flags, md_step), sizeof(long long));
+    if (st) return st;
+    free_graphs(sys);   // the step graphs hold the rule
     return HDMD_OK;
 }
 

@@ -117,6 +117,7 @@ def lib():
             "set_thermostat": [vp, dbl, dbl],
             "set_reference": [vp, vp],
             "set_barostat": [vp, dbl, dbl, dbl, i64],
+            "set_rebuild_rule": [vp, i32, i32],
             "get_box": [vp, C.POINTER(dbl)],
             "observables": [vp, dbl, i32, dbl, vp, vp],
             "fire_minimize": [vp, vp, vp],
@@ -279,6 +280,11 @@ def set_barostat(h, P_target, tau_P, beta=1.0, n_baro=10):
     _check(lib().set_barostat(h, float(P_target), float(tau_P), float(beta), int(n_baro)), h)
 
 
+def set_rebuild_rule(h, rule="exact", n_bet=1):
+    """List rebuild rule: "exact" (default) or the paper's, every n_bet steps."""
+    _check(lib().set_rebuild_rule(h, {"exact": 0, "paper": 1}[rule], int(n_bet)), h)
+
+
 def get_box(h):
     L = C.c_double()
     _check(lib().get_box(h, C.byref(L)), h)
@@ -383,6 +389,9 @@ class System:
 
     def box(self):
         return get_box(self.h)
+
+    def rebuild_rule(self, rule="exact", n_bet=1):
+        set_rebuild_rule(self.h, rule, n_bet)
 
     def set_reference(self, x_ref=None):
         set_reference(self.h, x_ref)

@@ -296,3 +296,22 @@ def test_seeded_swap_equals_oracle_draw(H):
         gs = g.state(sigma=True)["sigma"]
     assert nacc == total
     assert (gs == sig).all()
+
+
+def test_paper_rebuild_rule_matches_oracle(H):
+    """The paper's rule (Sec. II.C) every n_bet = 5 steps: the same rebuild
+    schedule as the oracle under that rule, hence the same (inexact) lists
+    and the same trajectory; calls in pieces keep the step count."""
+    s = W.make_system(3, 600, phi=0.5, dist="poly", T=0.05, seed=4)
+    ref = oracle.md_steps(s.x, s.v, s.sigma, s.L, 100, 0.005, rule="paper", n_bet=5)
+    for prec, tol in ((H.HDMD_FP64, 1e-9), (H.HDMD_MIXED, 1e-5)):
+        with H.System(3, s.L, s.sigma, s.x, s.v, precision=prec) as g:
+            g.rebuild_rule("paper", 5)
+            t1 = g.md_steps(37, 0.005)
+            t2 = g.md_steps(63, 0.005)
+            st = g.state()
+        assert t1["rebuilds"] + t2["rebuilds"] + 1 == ref["builds"]
+        dx = st["x"] - ref["x"]
+        dx -= s.L * np.round(dx / s.L)
+        assert np.abs(dx).max() < tol, (prec, np.abs(dx).max())
+        assert t2["E_pair"] == pytest.approx(ref["E"], rel=max(tol, 1e-11))
