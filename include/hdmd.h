@@ -213,6 +213,12 @@ hdmd_status set_barostat(hdmd_system *sys, double P_target, double tau_P, double
  * both sides, so forces may deviate from the exact ones.  FIRE keeps rule 0. */
 hdmd_status set_rebuild_rule(hdmd_system *sys, int rule, int n_bet);
 
+/* List radius: global 0 (default) keeps pair (i, j) in the lists when
+ * r < sigma_ij + s; global 1 uses the paper's single radius
+ * r_c^max = sigma_max + s (Sec. II.C) for every pair (longer lists, same
+ * forces).  The lists are rebuilt at once. */
+hdmd_status set_list_radius(hdmd_system *sys, int global);
+
 /* Current box side (it changes under the barostat). */
 hdmd_status get_box(hdmd_system *sys, double *L);
 

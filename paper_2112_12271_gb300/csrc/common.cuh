@@ -102,6 +102,7 @@ struct Dev {
     int32_t *cellid;        // subcell of each internal slot at the last build
     int32_t *batch_start;   // [ncells+1] exclusive scan of ceil(count / home_batch(d))
     float hmax_f;           // largest radius (sigma_max / 2)
+    double rglobal;         // > 0: one list radius sigma_max + s for every pair
     double *tx, *tv, *tsig, *tim;
     int32_t *timg, *tid;
     // lists

@@ -42,7 +42,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
         const float *ri = dv.gs0 + (size_t)i * RF;
 #pragma unroll
         for (int k = 0; k < D; ++k) xh[h][k] = ri[k];
-        rh[h] = ri[D] + skin;
+        rh[h] = (dv.rglobal > 0.0 ? dv.hmax_f : ri[D]) + skin;
         cnt[h] = 0;
     }
     const float reach_pad = dv.hmax_f;   // largest candidate radius
@@ -172,7 +172,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                                 r2 = fmaf(dx, dx, r2);
                             }
                         }
-                        const float rc = rh[h] + rj[D];
+                        const float rc = rh[h] + (dv.rglobal > 0.0 ? dv.hmax_f : rj[D]);
                         const float rc2 = rc * rc;
                         const float diff = r2 - rc2;
                         const float band = band_abs + 1e-5f * rc2;
@@ -186,7 +186,8 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                                 dx -= dv.L * rint(dx * dv.invL);
                                 s2d += dx * dx;
                             }
-                            const double rcd = 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                            const double rcd = dv.rglobal > 0.0 ? dv.rglobal
+                                                                : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
                             hit = s2d < rcd * rcd;
                         } else {
                             hit = diff < 0.f;

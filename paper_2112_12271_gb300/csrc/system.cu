@@ -1664,6 +1664,15 @@ hdmd_status set_rebuild_rule(hdmd_system *sys, int rule, int n_bet) {
     return HDMD_OK;
 }
 
+hdmd_status set_list_radius(hdmd_system *sys, int global) {
+    hdmd_status st = validate_sys(sys);
+    if (st) return st;
+    if (global != 0 && global != 1) return fail(sys, HDMD_E_INVALID, "global must be 0 or 1");
+    sys->dv.rglobal = global ? sys->sigma_max + sys->pot.skin : 0.0;
+    free_graphs(sys);   // the graphs hold the system description
+    return build_forced(sys, sys->buf);
+}
+
 hdmd_status get_box(hdmd_system *sys, double *L) {
     if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
     if (!L) return fail(sys, HDMD_E_INVALID, "L is NULL");

@@ -118,6 +118,7 @@ def lib():
             "set_reference": [vp, vp],
             "set_barostat": [vp, dbl, dbl, dbl, i64],
             "set_rebuild_rule": [vp, i32, i32],
+            "set_list_radius": [vp, i32],
             "get_box": [vp, C.POINTER(dbl)],
             "observables": [vp, dbl, i32, dbl, vp, vp],
             "fire_minimize": [vp, vp, vp],
@@ -392,6 +393,10 @@ class System:
 
     def rebuild_rule(self, rule="exact", n_bet=1):
         set_rebuild_rule(self.h, rule, n_bet)
+
+    def list_radius(self, global_radius=False):
+        """Per-pair list radius sigma_ij + s, or the paper's sigma_max + s."""
+        _check(lib().set_list_radius(self.h, int(bool(global_radius))), self.h)
 
     def set_reference(self, x_ref=None):
         set_reference(self.h, x_ref)

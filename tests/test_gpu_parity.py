@@ -315,3 +315,30 @@ def test_paper_rebuild_rule_matches_oracle(H):
         dx -= s.L * np.round(dx / s.L)
         assert np.abs(dx).max() < tol, (prec, np.abs(dx).max())
         assert t2["E_pair"] == pytest.approx(ref["E"], rel=max(tol, 1e-11))
+
+
+@pytest.mark.parametrize("d,N,L", [(3, 1000, 11.78), (6, 1500, 4.4), (8, 600, 3.1)])
+def test_global_list_radius_matches_oracle(H, d, N, L):
+    """The paper's single list radius sigma_max + s (Sec. II.C): the lists
+    equal the oracle's global-radius lists (ties within 1e-6 excepted) and
+    the forces are unchanged."""
+    rng = np.random.default_rng(d)
+    x = W.uniform_positions(rng, N, d, L)
+    sigma = W.polydisperse(rng, N)
+    ref = oracle.neighbors_brute(x, sigma, L, 0.3, global_cut=True)
+    rc = sigma.max() + 0.3
+    for prec, tol in ((H.HDMD_FP64, 1e-12), (H.HDMD_MIXED, 1e-5)):
+        with H.System(d, L, sigma, x, precision=prec) as g:
+            F0, E0, _ = g.forces()
+            g.list_radius(True)
+            got = g.neighbors()
+            F1, E1, _ = g.forces()
+        gs, rs = oracle.lists_as_sets(*got), oracle.lists_as_sets(*ref)
+        for i, (a, b) in enumerate(zip(gs, rs)):
+            for j in a ^ b:
+                dx = x[j] - x[i]
+                dx -= L * np.round(dx / L)
+                assert abs(np.sqrt(dx @ dx) - rc) <= TIE, (i, j)
+        assert got[0].sum() > 0
+        # the same pairs interact; only the summation order changes
+        assert np.abs(F1 - F0).max() <= tol * max(np.abs(F0).max(), 1e-300)
