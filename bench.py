@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -122,9 +123,25 @@ def oracle_md_sample(sysd, nsteps):
     return dt, out
 
 
+def host_cpu():
+    """CPU model and logical core count of this host (for the baseline record)."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    model = "%s (%s)" % (line.split(":", 1)[1].strip(), platform.machine())
+                    break
+    except OSError:
+        pass
+    return {"cpu": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(sysd, nsteps=100):
     dt, _ = oracle_md_sample(sysd, nsteps)
     return {"value": sysd.N * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            **host_cpu(),
             "sample": "%d VV timesteps of the same d=6 N=32768 system (one cell-list "
                       "build + %d force evaluations), serial FP64 C, %.1f s" % (nsteps, nsteps, dt)}
 
@@ -149,6 +166,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "N": s.N, "d": 6,
                        "timesteps_per_step": per, "l2": "cpu"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             **host_cpu(),
                              "sample": "%d VV timesteps per step, serial FP64 C oracle "
                                        "(list build each step)" % per},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

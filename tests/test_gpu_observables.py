@@ -59,3 +59,22 @@ def test_explicit_reference_and_errors(H):
         assert r["f_ov"] == 1.0
         with pytest.raises(H.HDMDError):
             g.observables(nbins=10, r_max=0.0)
+
+
+def test_long_run_msd_agrees_with_oracle_statistically(H):
+    """Beyond a few hundred steps trajectories part (chaos), so long runs are
+    compared by statistics: after 3000 steps of a d = 3 soft-sphere liquid
+    the GPU's mean squared displacement is within 10 % of the oracle's, in
+    FP64 and mixed precision, and energy is conserved to the same order."""
+    s = W.make_system(3, 1000, phi=0.45, dist="poly", T=0.05, seed=12)
+    ref = oracle.md_steps(s.x, s.v, s.sigma, s.L, 3000, 0.005)
+    ru = ref["x"] + s.L * ref["img"]
+    msd_ref = float(((ru - s.x) ** 2).sum(axis=1).mean())
+    assert msd_ref > 0.05                     # the atoms have moved well beyond rattling
+    for prec in (H.HDMD_FP64, H.HDMD_MIXED):
+        with H.System(3, s.L, s.sigma, s.x, s.v, precision=prec) as g:
+            g.set_reference()
+            t = g.md_steps(3000, 0.005)
+            msd = g.observables()["msd"]
+        assert msd == pytest.approx(msd_ref, rel=0.10), (prec, msd, msd_ref)
+        assert t["E_pair"] + t["K"] == pytest.approx(ref["E"] + ref["K"], rel=1e-3)
