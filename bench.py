@@ -195,7 +195,8 @@ def run_gpu(args):
         torch.distributed.barrier()
         B.build()
 
-    s = W.c1_poly_d6(seed=rank, N=WORKLOADS[args.workload])
+    from paper_2112_12271_gb300 import replicas
+    s = W.c1_poly_d6(seed=replicas.replica_seed(rank), N=WORKLOADS[args.workload])
     md_per_step = args.md_per_step
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -231,12 +232,7 @@ def run_gpu(args):
     ms, rebuilds, last = timed_md(g, args.steps, args.warmup)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    total_ms = sum(ms)
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = ws * s.N * md_per_step * args.steps / (total_ms / 1000.0)
+    value, total_ms = replicas.aggregate(s.N * md_per_step * args.steps, sum(ms), device=dev)
     info = g.info()
     prof = g.profile(reps=50, dt=DT) if not args.no_profile else None
 
