@@ -403,7 +403,9 @@ def run_paper(args):
     move capped at 0.01), given velocities at T, then run for
     args.paper_tau time units of NVT MD (Berendsen, tau_T = 0.5)
     (625 steps each) with one SWAP pass (p = 0.1) per time unit.  Reports
-    atom-steps/s per d and the device time per list entry and step."""
+    atom-steps/s per d, the device time per list entry and step, and the
+    split of the device time over leapfrog, list builds, minimisation (one
+    FIRE per 10 time units, counted pro rata) and SWAP, as in Table IV."""
     import torch
     from paper_2112_12271_gb300 import build as B
     from paper_2112_12271_gb300 import hdmd
@@ -431,17 +433,43 @@ def run_paper(args):
             torch.cuda.synchronize()
             a.record(stream)
             acc = reb = 0
+            swap_ms = 0.0
             for tau in range(args.paper_tau):
                 t = g.md_steps(steps_per_tau, W.PAPER_DT)
                 reb += t["rebuilds"]
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
                 acc += g.swap(W.PAPER_T, p=0.1, nsweeps=1, seed=1000 * d + tau)[0]
+                e1.record(stream)
+                e1.synchronize()
+                swap_ms += e0.elapsed_time(e1)
             c.record(stream)
             c.synchronize()
             sec = a.elapsed_time(c) / 1000.0
             info = g.info()
+            prof = g.profile(reps=20, dt=W.PAPER_DT)
             t0 = time.perf_counter()
             obs = g.observables(nbins=100, r_max=2.0)
             obs_ms = 1000.0 * (time.perf_counter() - t0)
+            st = g.state(v=False, img=False, sigma=True)   # SWAP moved the diameters
+        # one energy minimisation of the current configuration per 10 time
+        # units, as in the paper's runs (FIRE to E_pair/N < 1e-25), on a copy
+        with hdmd.System(d, s.L, st["sigma"], st["x"], None, st["sigma"] ** d,
+                         precision=hdmd.HDMD_MIXED, **law) as gm:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mres = gm.fire(e_thres=1e-25, dt0=W.PAPER_DT, dt_max=10 * W.PAPER_DT,
+                           dt_min=0.02 * W.PAPER_DT, max_iter=200000)
+            e1.record(stream)
+            e1.synchronize()
+            min_ms = e0.elapsed_time(e1) * args.paper_tau / 10.0
+        vl_ms = reb * prof["rebuild_ms"]
+        md_ms = 1000.0 * sec - swap_ms
+        whole = 1000.0 * sec + min_ms
+        shares = {"leapfrog": (md_ms - vl_ms) / whole, "vl_build": vl_ms / whole,
+                  "minimisation": min_ms / whole, "swap": swap_ms / whole}
         n_steps = steps_per_tau * args.paper_tau
         z = info["total_list_entries"] / s.N
         rows.append({"d": d, "N": s.N, "phi_star": W.PHI_STAR[d], "L": s.L, "n_cell": info["n_cell"],
@@ -451,7 +479,10 @@ def run_paper(args):
                      "mean_list_length": z, "rebuilds": reb, "swap_accepted": acc,
                      "T_end": t["T"], "E_pair_per_atom": t["E_pair"] / s.N,
                      "msd": obs["msd"], "alpha2": obs["alpha2"], "f_ov": obs["f_ov"],
-                     "Z": obs["Z"], "observables_ms": obs_ms})
+                     "Z": obs["Z"], "observables_ms": obs_ms,
+                     "minimisation": {"iterations": mres["iterations"], "ms": min_ms * 10.0 / args.paper_tau,
+                                      "E_pair_per_atom": mres["E_pair"] / s.N},
+                     "runtime_share": shares})
         total_atom_steps += s.N * n_steps
         total_s += sec
         print(json.dumps({"paper_row": rows[-1]}), file=sys.stderr, flush=True)
