@@ -30,7 +30,10 @@ namespace hdmd {
 
 constexpr int kMaxD = 10;
 constexpr int kNRed = 16;          // reduction slots per block
-constexpr int kStepNT = 128;       // threads per block of the force / update kernels
+#ifndef HDMD_STEP_NT
+#define HDMD_STEP_NT 128
+#endif
+constexpr int kStepNT = HDMD_STEP_NT;   // threads per block of the force / update kernels
 constexpr int kMaxLanes = 32;      // largest lanes-per-atom group
 
 // reduction slots
