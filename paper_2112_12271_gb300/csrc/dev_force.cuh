@@ -164,8 +164,9 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
                     r2 = fmaf(t, t, r2);
                 }
                 const float s = hi + rj[u][D];
-                if (r2 < s * s && r2 > 0.f) {
-                    const float rinv = rsqrtf(r2);
+                if (r2 < s * s) {
+                    // coincident atoms: no force (direction undefined), U(0)
+                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                     const float r = r2 * rinv;
                     const float ee = eps_pair<D, float>(eps, hi, rj[u][D], scale);
                     if constexpr (LAW == 2) {
