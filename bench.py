@@ -570,7 +570,8 @@ def run_serve(args):
     warm = W.c4_requests(duration=0.05, rate=200.0, seed=1)
     warm_sys = [W.c4_system(r) for r in warm]
     srv = serve.Server(precision=hdmd.HDMD_MIXED, slots=args.slots, small_N=args.small_n,
-                       batch_pool_bytes=args.pool_gb << 30, budget=args.budget)
+                       batch_pool_bytes=args.pool_gb << 30, budget=args.budget,
+                       policy=args.policy)
     srv.run(warm, warm_sys)            # warm-up: builds, graphs, allocator
     recs = srv.run(reqs, systems, time_limit=args.serve_time_limit)
     srv.close()
@@ -578,7 +579,8 @@ def run_serve(args):
     k = min(args.seq_sample, len(reqs))
     seq = serve.summarize(serve.sequential_fp64(reqs[:k], systems[:k]))
     srv2 = serve.Server(precision=hdmd.HDMD_MIXED, slots=args.slots, small_N=args.small_n,
-                        batch_pool_bytes=args.pool_gb << 30, budget=args.budget)
+                        batch_pool_bytes=args.pool_gb << 30, budget=args.budget,
+                        policy=args.policy)
     sub = serve.summarize(srv2.run(reqs[:k], systems[:k]))
     srv2.close()
     md_work = sum(r["N"] * r["nsteps"] for r in reqs if r["kind"] == 0)
@@ -590,7 +592,7 @@ def run_serve(args):
             "config": {"workload": "serve_poisson200_md_fire_d3-8_N256-131072",
                        "requests": len(reqs), "arrival_seconds": args.serve_seconds,
                        "md_atom_steps": md_work, "budget_per_launch": args.budget,
-                       "slots": args.slots, "small_N": args.small_n},
+                       "slots": args.slots, "small_N": args.small_n, "policy": args.policy},
             "latency_p50_s": summ["p50_s"], "latency_p99_s": summ["p99_s"], "summary": summ,
             "first_%d_requests" % k: {"server": sub, "sequential_fp64": seq}}
     print(json.dumps(line), flush=True)
@@ -622,6 +624,8 @@ def main():
                     help="serving workload: steps / FIRE iterations per job per launch")
     ap.add_argument("--pool-gb", type=int, default=2,
                     help="serving workload: batched-engine device pool (GiB)")
+    ap.add_argument("--policy", default="fifo", choices=["fifo", "sjf"],
+                    help="serving workload: admission order of waiting systems")
     ap.add_argument("--slots", type=int, default=16,
                     help="serving workload: concurrent system jobs")
     ap.add_argument("--small-n", type=int, default=1024,

@@ -8,8 +8,9 @@ overlaps on the device:
 
 * a job with N > small_N runs as its own system (``hdmd.System``, the
   grid-wide kernels and CUDA graphs) on its own CUDA stream, in one of
-  ``slots`` worker threads.  It is admitted, first come first served, when a
-  slot is free and its device footprint (``hdmd.system_footprint``, with
+  ``slots`` worker threads.  It is admitted (first come first served, or
+  with policy "sjf" smallest estimated work first) when a slot is free and
+  its device footprint (``hdmd.system_footprint``, with
   head-room for list growth) fits in what the running systems leave of the
   device-memory budget (by default 85 % of the free HBM at start, less the
   batch pool);
@@ -60,11 +61,21 @@ class Record:
         return None if self.done is None else self.done - self.arrival
 
 
+def work(req, fire_iterations=500):
+    """Estimated work of a request in atom-steps (FIRE: a typical iteration
+    count), the key of the shortest-job-first policy."""
+    steps = req.get("nsteps", 0) if req["kind"] == hdmd.JOB_MD else fire_iterations
+    return req["N"] * steps
+
+
 class Server:
     def __init__(self, precision=hdmd.HDMD_MIXED, slots=16, small_N=1024,
                  batch_pool_bytes=2 << 30, max_batch_jobs=2048, mem_bytes=None,
                  budget=256, dt=0.005, max_iter=20000, keep_positions=False,
-                 headroom=1.5, log=None):
+                 headroom=1.5, log=None, policy="fifo"):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
         import torch
         self.torch = torch
         self.precision = precision
@@ -165,7 +176,13 @@ class Server:
                 while pending and requests[pending[0]]["t"] <= now:
                     rec = recs[pending.popleft()]
                     rec.arrival = rec.req["t"]
-                    (small_q if rec.req["N"] <= self.small_N else big_q).append(rec)
+                    if rec.req["N"] <= self.small_N:
+                        small_q.append(rec)
+                    elif self.policy == "sjf":   # keep the waiting systems by estimated work
+                        big_q.append(rec)
+                        big_q = collections.deque(sorted(big_q, key=lambda r: (work(r.req), r.idx)))
+                    else:
+                        big_q.append(rec)
                 # retire finished systems, returning their memory reservation
                 still = []
                 for rec, f in in_flight:
