@@ -113,8 +113,8 @@ size_t layout(Dev &dv, char *base, int cap) {
 
 struct hdmd_batch {
     cudaStream_t stream = nullptr;
-    cudaStream_t fork[kMaxD + 1] = {nullptr};
-    cudaEvent_t ev_fork = nullptr, ev_join[kMaxD + 1] = {nullptr};
+    cudaStream_t fork[2 * (kMaxD + 1)] = {nullptr};       // [d]: normal, [kMaxD + 1 + d]: wide
+    cudaEvent_t ev_fork = nullptr, ev_join[2 * (kMaxD + 1)] = {nullptr};
     int prec = HDMD_MIXED;
     char *pool_dev = nullptr;
     Pool pool;
@@ -156,6 +156,22 @@ void launch_one(int d, BatchJob *jobs, const int *order, BatchCtl *ctl, int grid
         case 8: launch_batch_d8(jobs, order, ctl, grid, s); break;
         case 9: launch_batch_d9(jobs, order, ctl, grid, s); break;
         case 10: launch_batch_d10(jobs, order, ctl, grid, s); break;
+        default: break;
+    }
+}
+
+void launch_one_wide(int d, BatchJob *jobs, const int *order, BatchCtl *ctl, int grid,
+                     cudaStream_t s) {
+    switch (d) {
+        case 2: launch_batch_wide_d2(jobs, order, ctl, grid, s); break;
+        case 3: launch_batch_wide_d3(jobs, order, ctl, grid, s); break;
+        case 4: launch_batch_wide_d4(jobs, order, ctl, grid, s); break;
+        case 5: launch_batch_wide_d5(jobs, order, ctl, grid, s); break;
+        case 6: launch_batch_wide_d6(jobs, order, ctl, grid, s); break;
+        case 7: launch_batch_wide_d7(jobs, order, ctl, grid, s); break;
+        case 8: launch_batch_wide_d8(jobs, order, ctl, grid, s); break;
+        case 9: launch_batch_wide_d9(jobs, order, ctl, grid, s); break;
+        case 10: launch_batch_wide_d10(jobs, order, ctl, grid, s); break;
         default: break;
     }
 }
@@ -212,19 +228,20 @@ hdmd_status batch_create(int64_t pool_bytes, int max_jobs, hdmd_precision prec, 
     b->pool.init((size_t)pool_bytes);
     if (cudaMalloc((void **)&b->d_jobs, sizeof(BatchJob) * max_jobs) != cudaSuccess ||
         cudaMalloc((void **)&b->d_order, sizeof(int) * max_jobs) != cudaSuccess ||
-        cudaMalloc((void **)&b->d_ctl, sizeof(BatchCtl) * (kMaxD + 1)) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_ctl, sizeof(BatchCtl) * 2 * (kMaxD + 1)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_jobs, sizeof(BatchJob) * max_jobs) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_order, sizeof(int) * max_jobs) != cudaSuccess ||
-        cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl) * (kMaxD + 1)) != cudaSuccess) {
+        cudaMallocHost((void **)&b->h_ctl, sizeof(BatchCtl) * 2 * (kMaxD + 1)) != cudaSuccess) {
         cudaGetLastError();
         return bail(bfail(b, HDMD_E_NOMEM, "batch tables"));
     }
     std::memset(b->h_jobs, 0, sizeof(BatchJob) * max_jobs);
     if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return bail(bfail(b, HDMD_E_CUDA, "event"));
-    for (int d = 2; d <= kMaxD; ++d) {
-        if (cudaStreamCreateWithFlags(&b->fork[d], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->ev_join[d], cudaEventDisableTiming) != cudaSuccess) {
+    for (int k = 0; k < 2 * (kMaxD + 1); ++k) {
+        if (k % (kMaxD + 1) < 2) continue;
+        if (cudaStreamCreateWithFlags(&b->fork[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return bail(bfail(b, HDMD_E_CUDA, "streams"));
         }
@@ -385,43 +402,57 @@ hdmd_status batch_run(hdmd_batch *b, int64_t budget, int *n_unfinished) {
     if (!b) return bfail(nullptr, HDMD_E_INVALID, "null batch");
     if (budget < 0) return bfail(b, HDMD_E_INVALID, "budget must be >= 0");
     // queues per dimension, largest job first
+    // (the jobs above kBatchWideN atoms, at the head of each queue, run in the
+    // wide blocks of their own kernel: ctl[kMaxD + 1 + d])
     std::vector<std::vector<int>> per(kMaxD + 1);
     for (int k = 0; k < b->max_jobs; ++k)
         if (b->jobs[k].live && b->h_jobs[k].status == JOB_ACTIVE) per[b->jobs[k].d].push_back(k);
-    unsigned dims = 0;
+    unsigned dims = 0, wdims = 0;
     int pos = 0;
     for (int d = 2; d <= kMaxD; ++d) {
         auto &q = per[d];
         std::stable_sort(q.begin(), q.end(), [&](int a, int c) { return b->jobs[a].N > b->jobs[c].N; });
-        b->h_ctl[d].first = pos;
-        b->h_ctl[d].njobs = (int)q.size();
-        b->h_ctl[d].next = 0;
-        b->h_ctl[d].budget = budget;
+        int nw = 0;
+        while (nw < (int)q.size() && b->jobs[q[nw]].N > kBatchWideN) ++nw;
+        BatchCtl &cw = b->h_ctl[kMaxD + 1 + d], &cn = b->h_ctl[d];
+        cw.first = pos;
+        cw.njobs = nw;
+        cw.next = 0;
+        cw.budget = budget;
+        cn.first = pos + nw;
+        cn.njobs = (int)q.size() - nw;
+        cn.next = 0;
+        cn.budget = budget;
         for (size_t k = 0; k < q.size(); ++k) b->h_order[pos + k] = q[k];
-        if (!q.empty()) dims |= 1u << d;
+        if (cn.njobs > 0) dims |= 1u << d;
+        if (nw > 0) wdims |= 1u << d;
         pos += (int)q.size();
     }
-    if (!dims) {
+    if (!dims && !wdims) {
         if (n_unfinished) *n_unfinished = 0;
         return HDMD_OK;
     }
     cudaStream_t s = b->stream;
     BCK(cudaMemcpyAsync(b->d_order, b->h_order, sizeof(int) * std::max(pos, 1), cudaMemcpyHostToDevice, s));
-    BCK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl) * (kMaxD + 1), cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl) * 2 * (kMaxD + 1), cudaMemcpyHostToDevice, s));
     auto run_direct = [&]() -> hdmd_status {
         BCK(cudaEventRecord(b->ev_fork, s));
-        for (int d = 2; d <= kMaxD; ++d) {
-            if (!(dims & (1u << d))) continue;
-            BCK(cudaStreamWaitEvent(b->fork[d], b->ev_fork, 0));
-            launch_one(d, b->d_jobs, b->d_order, b->d_ctl + d, grid_for(b), b->fork[d]);
+        for (int k = 0; k < 2 * (kMaxD + 1); ++k) {
+            const bool wide = k > kMaxD;
+            const int d = wide ? k - (kMaxD + 1) : k;
+            if (d < 2 || !((wide ? wdims : dims) & (1u << d))) continue;
+            BCK(cudaStreamWaitEvent(b->fork[k], b->ev_fork, 0));
+            if (wide) launch_one_wide(d, b->d_jobs, b->d_order, b->d_ctl + k, b->nsm, b->fork[k]);
+            else launch_one(d, b->d_jobs, b->d_order, b->d_ctl + k, grid_for(b), b->fork[k]);
             BCK(cudaGetLastError());
-            BCK(cudaEventRecord(b->ev_join[d], b->fork[d]));
-            BCK(cudaStreamWaitEvent(s, b->ev_join[d], 0));
+            BCK(cudaEventRecord(b->ev_join[k], b->fork[k]));
+            BCK(cudaStreamWaitEvent(s, b->ev_join[k], 0));
         }
         return HDMD_OK;
     };
     hdmd_status st = HDMD_OK;
-    const unsigned key = dims;   // kernel arguments depend only on which dimensions run
+    // kernel arguments depend only on which dimensions (and block classes) run
+    const unsigned key = dims | (wdims << 16);
     bool launched = false;
     if (b->use_graphs) {
         auto it = b->graphs.find(key);
@@ -609,9 +640,9 @@ hdmd_status batch_destroy(hdmd_batch *b) {
         cudaGraphExecDestroy(kv.second.second);
         cudaGraphDestroy(kv.second.first);
     }
-    for (int d = 0; d <= kMaxD; ++d) {
-        if (b->fork[d]) cudaStreamDestroy(b->fork[d]);
-        if (b->ev_join[d]) cudaEventDestroy(b->ev_join[d]);
+    for (int k = 0; k < 2 * (kMaxD + 1); ++k) {
+        if (b->fork[k]) cudaStreamDestroy(b->fork[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
     }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->pool_dev) cudaFree(b->pool_dev);

@@ -35,7 +35,9 @@ struct BatchCtl {
     long long budget;     // iterations (FIRE) or steps (MD) per job per launch; 0 = to the end
 };
 
-constexpr int kBatchNT = 256;   // threads per job block
+constexpr int kBatchNT = 256;       // threads per job block
+constexpr int kBatchWideNT = 512;   // threads per block of the large jobs
+constexpr int kBatchWideN = 4096;   // jobs with more atoms run in the wide blocks
 
 // persistent kernel over the jobs of dimension D listed in order[0..ctl->njobs),
 // and the timing probe of the lanes-per-atom autotuner (builds the job's lists
@@ -43,6 +45,8 @@ constexpr int kBatchNT = 256;   // threads per job block
 #define HDMD_BATCH_DECLARE(D)                                                          \
     void launch_batch_d##D(BatchJob *jobs, const int *order, BatchCtl *ctl, int grid,  \
                            cudaStream_t s);                                            \
+    void launch_batch_wide_d##D(BatchJob *jobs, const int *order, BatchCtl *ctl,       \
+                                int grid, cudaStream_t s);                             \
     void launch_batch_probe_d##D(BatchJob *job, int reps, cudaStream_t s);
 HDMD_BATCH_DECLARE(2)
 HDMD_BATCH_DECLARE(3)

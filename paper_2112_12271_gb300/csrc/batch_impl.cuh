@@ -26,8 +26,12 @@
 namespace hdmd {
 namespace {
 
-constexpr int BT = kBatchNT;
-constexpr int NWB = BT / 32;
+// The block size is the launch's (kBatchNT, or kBatchWideNT for the jobs
+// above kBatchWideN atoms): a job always runs in blocks of the same size, so
+// its reductions, and its result, do not depend on the rest of the batch.
+#define BT ((int)blockDim.x)
+#define NWB ((int)(blockDim.x >> 5))
+constexpr int kMaxWarpsB = 32;
 
 __device__ __forceinline__ double blk_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -239,7 +243,7 @@ __device__ double blk_kick(const Dev &dv, double halfdt, double dt, bool drift, 
 template <int D>
 __device__ void run_job(BatchJob &J, long long budget) {
     __shared__ Dev sdv;
-    __shared__ double sh[NWB];
+    __shared__ double sh[kMaxWarpsB];
     __shared__ int s_st;
     if (threadIdx.x == 0) {
         sdv = J.dv;
@@ -331,7 +335,7 @@ __device__ void run_job(BatchJob &J, long long budget) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(BT, 2) k_batch(BatchJob *jobs, const int *order, BatchCtl *ctl) {
+__device__ __forceinline__ void batch_queue(BatchJob *jobs, const int *order, BatchCtl *ctl) {
     __shared__ int s_q;
     for (;;) {
         if (threadIdx.x == 0) s_q = atomicAdd(&ctl->next, 1);
@@ -344,9 +348,20 @@ __global__ void __launch_bounds__(BT, 2) k_batch(BatchJob *jobs, const int *orde
 }
 
 template <int D>
-__global__ void __launch_bounds__(BT, 2) k_batch_probe(BatchJob *job, int reps) {
+__global__ void __launch_bounds__(kBatchNT, 2) k_batch(BatchJob *jobs, const int *order, BatchCtl *ctl) {
+    batch_queue<D>(jobs, order, ctl);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBatchWideNT, 1) k_batch_wide(BatchJob *jobs, const int *order,
+                                                               BatchCtl *ctl) {
+    batch_queue<D>(jobs, order, ctl);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBatchNT, 2) k_batch_probe(BatchJob *job, int reps) {
     __shared__ Dev sdv;
-    __shared__ double sh[NWB];
+    __shared__ double sh[kMaxWarpsB];
     BatchJob &J = *job;
     if (threadIdx.x == 0) {
         sdv = J.dv;
@@ -375,10 +390,16 @@ __global__ void __launch_bounds__(BT, 2) k_batch_probe(BatchJob *job, int reps) 
 #define HDMD_BATCH_INSTANTIATE(D)                                                      \
     void launch_batch_d##D(BatchJob *jobs, const int *order, BatchCtl *ctl, int grid,  \
                            cudaStream_t s) {                                           \
-        k_batch<D><<<grid, BT, 0, s>>>(jobs, order, ctl);                              \
+        k_batch<D><<<grid, kBatchNT, 0, s>>>(jobs, order, ctl);                        \
+    }                                                                                  \
+    void launch_batch_wide_d##D(BatchJob *jobs, const int *order, BatchCtl *ctl,       \
+                                int grid, cudaStream_t s) {                            \
+        k_batch_wide<D><<<grid, kBatchWideNT, 0, s>>>(jobs, order, ctl);               \
     }                                                                                  \
     void launch_batch_probe_d##D(BatchJob *job, int reps, cudaStream_t s) {            \
-        k_batch_probe<D><<<1, BT, 0, s>>>(job, reps);                                  \
+        k_batch_probe<D><<<1, kBatchNT, 0, s>>>(job, reps);                            \
     }
 
 }  // namespace hdmd
+#undef BT
+#undef NWB
