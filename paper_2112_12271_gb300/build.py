@@ -20,7 +20,8 @@ LIB_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIB_DIR, "libhdmd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["kernels_bin.cu", "kernels_nbr.cu", "kernels_force.cu", "kernels_swap.cu",
-         "kernels_batch_lo.cu", "kernels_batch_d6.cu", "kernels_batch_d8.cu", "system.cu",
+         "kernels_batch_d2.cu", "kernels_batch_d4.cu", "kernels_batch_d6.cu",
+         "kernels_batch_d8.cu", "kernels_batch_d9.cu", "system.cu",
          "batch.cu", "noalloc.cu", "kernels_obs.cu"]
 
 

@@ -1,8 +1,6 @@
-// kernels_batch_d8.cu -- batched-job kernels for d = 8..10 (see batch_impl.cuh).
+// kernels_batch_d8.cu -- batched-job kernels for d = 8 (see batch_impl.cuh).
 #include "batch_impl.cuh"
 
 namespace hdmd {
 HDMD_BATCH_INSTANTIATE(8)
-HDMD_BATCH_INSTANTIATE(9)
-HDMD_BATCH_INSTANTIATE(10)
 }  // namespace hdmd
