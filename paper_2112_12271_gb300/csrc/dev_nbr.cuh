@@ -53,13 +53,14 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
     const unsigned allh = (1u << nh) - 1u;
 
     // rows of the stencil, 32 at a time: lane l works out row sr0 + l (its
-    // subcell index, offset code and which home atoms can reach it), then
-    // the warp walks the reachable rows one by one
+    // subcell index, offset code, which home atoms can reach it and where its
+    // atoms lie), then the warp walks the reachable rows one by one
     for (int sr0 = 0; sr0 < Srow; sr0 += 32) {
         const int sr = sr0 + lane;
         int Jrow = 0;
         uint32_t rcode = 0;
         unsigned amask = 0;
+        int ps1 = 0, pl1 = 0, ps2 = 0, pl2 = 0, ps3 = 0, pl3 = 0;   // the row's pieces
         if (sr < Srow) {
             int off[D];
             int rem = sr;
@@ -90,6 +91,22 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
             } else {
                 amask = allh;
             }
+            // the row's subcells along the last axis as up to three pieces,
+            // looked up here for all 32 rows at once (one round trip) rather
+            // than row after row in the walk below
+            if (amask) {
+                if (WRAP) {
+                    ps1 = dv.cell_start[Jrow + cl_m]; pl1 = dv.cell_start[Jrow + cl_m + 1] - ps1;
+                    ps2 = dv.cell_start[Jrow + cl];   pl2 = dv.cell_start[Jrow + cl + 1] - ps2;
+                    ps3 = dv.cell_start[Jrow + cl_p]; pl3 = dv.cell_start[Jrow + cl_p + 1] - ps3;
+                } else if (n == 2) {
+                    ps1 = dv.cell_start[Jrow + cl];     pl1 = dv.cell_start[Jrow + cl + 1] - ps1;
+                    ps2 = dv.cell_start[Jrow + 1 - cl]; pl2 = dv.cell_start[Jrow + 2 - cl] - ps2;
+                } else {   // one subcell: every atom
+                    ps1 = dv.cell_start[0]; pl1 = dv.cell_start[1] - ps1;
+                    ps2 = ps1;
+                }
+            }
         }
         unsigned rows = __ballot_sync(0xffffffffu, amask != 0);
         while (rows) {
@@ -102,19 +119,10 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
 #pragma unroll
             for (int k = 0; k < D - 1; ++k) offL[k] = (float)((int)((rc0 >> (2 * k)) & 3u) - 1) * Lsc;
             // the row's subcells along the last axis, as up to three pieces
-            int s1, l1, s2, l2, s3 = 0, l3 = 0;
-            int o1, o2, o3 = 1;
-            if (WRAP) {
-                s1 = dv.cell_start[Jr + cl_m]; l1 = dv.cell_start[Jr + cl_m + 1] - s1; o1 = -1;
-                s2 = dv.cell_start[Jr + cl];   l2 = dv.cell_start[Jr + cl + 1] - s2;   o2 = 0;
-                s3 = dv.cell_start[Jr + cl_p]; l3 = dv.cell_start[Jr + cl_p + 1] - s3; o3 = 1;
-            } else if (n == 2) {
-                s1 = dv.cell_start[Jr + cl];     l1 = dv.cell_start[Jr + cl + 1] - s1;     o1 = 0;
-                s2 = dv.cell_start[Jr + 1 - cl]; l2 = dv.cell_start[Jr + 2 - cl] - s2; o2 = 1;
-            } else {   // one subcell: every atom
-                s1 = dv.cell_start[0]; l1 = dv.cell_start[1] - s1; o1 = 0;
-                s2 = s1; l2 = 0; o2 = 0;
-            }
+            const int s1 = __shfl_sync(0xffffffffu, ps1, src), l1 = __shfl_sync(0xffffffffu, pl1, src);
+            const int s2 = __shfl_sync(0xffffffffu, ps2, src), l2 = __shfl_sync(0xffffffffu, pl2, src);
+            const int s3 = __shfl_sync(0xffffffffu, ps3, src), l3 = __shfl_sync(0xffffffffu, pl3, src);
+            const int o1 = WRAP ? -1 : 0, o2 = WRAP ? 0 : (n == 2 ? 1 : 0), o3 = 1;
             const int tot = l1 + l2 + l3;
             for (int t0 = 0; t0 < tot; t0 += 32) {
                 const int t = t0 + lane;
