@@ -46,6 +46,26 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
         cnt[h] = 0;
     }
     const float reach_pad = dv.hmax_f;   // largest candidate radius
+    // n_cell >= 3: the test below is written as
+    //   |r_j - x_h|^2 - (rho_j + rho_h)^2
+    //     = (|r_j|^2 - rho_j^2) + (|x_h|^2 - rho_h^2) - 2 (r_j . x_h + rho_j rho_h),
+    // the first bracket once per candidate, the second once per home atom, so
+    // a pair test is d + 3 operations.  Its rounding error is below
+    // (d + 3) u S with S = sum_k (|r_jk| + |x_hk|)^2 + (rho_j + rho_h)^2
+    // <= (4d + 1) L_sc^2 (|x_hk| <= L_sc/2, |r_jk| <= 3 L_sc/2, rho_j + rho_h
+    // <= L_sc); twice that widens the guard band, which stays far below
+    // L_sc^2, so the FP64 recheck remains rare.
+    float Bh[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        float b = -rh[h] * rh[h];
+#pragma unroll
+        for (int k = 0; k < D; ++k) b = fmaf(xh[h][k], xh[h][k], b);
+        Bh[h] = b;
+    }
+    const float rcmax = 2.f * dv.hmax_f + skin;   // largest cutoff
+    const float band_x = fmaf(1e-5f, rcmax * rcmax, band_abs)
+                       + (float)((D + 3) * (4 * D + 1)) * 1.2e-7f * Lsc * Lsc;
     const int base = WRAP ? 3 : (n == 1 ? 1 : 2);   // distinct offsets per axis
     const int Srow = pow_int(base, D - 1);
     const int cl = C[D - 1];
@@ -112,7 +132,6 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
         while (rows) {
             const int src = __ffs(rows) - 1;
             rows &= rows - 1;
-            const int Jr = __shfl_sync(0xffffffffu, Jrow, src);
             const uint32_t rc0 = __shfl_sync(0xffffffffu, rcode, src);
             const unsigned active = __shfl_sync(0xffffffffu, amask, src);
             float offL[D];   // offsets of axes 0..D-2 times L_sc (WRAP)
@@ -141,10 +160,15 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                         rj[4 * q] = tt.x; rj[4 * q + 1] = tt.y; rj[4 * q + 2] = tt.z; rj[4 * q + 3] = tt.w;
                     }
                 }
+                float rhoj = 0.f, Aj = 0.f;
                 if (WRAP) {
 #pragma unroll
                     for (int k = 0; k < D - 1; ++k) rj[k] += offL[k];
                     rj[D - 1] = fmaf((float)olast, Lsc, rj[D - 1]);
+                    rhoj = dv.rglobal > 0.0 ? dv.hmax_f : rj[D];
+                    Aj = -rhoj * rhoj;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) Aj = fmaf(rj[k], rj[k], Aj);
                 }
                 const uint32_t wcode = WRAP ? (rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)))) : 0u;
 #pragma unroll
@@ -154,14 +178,15 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                     bool hit = false;
                     uint32_t code = wcode;
                     if (okj && j != i) {
-                        float r2 = 0.f;
+                        float diff, band;
                         if (WRAP) {
+                            float dot = rhoj * rh[h];
 #pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                const float dx = rj[k] - xh[h][k];
-                                r2 = fmaf(dx, dx, r2);
-                            }
+                            for (int k = 0; k < D; ++k) dot = fmaf(rj[k], xh[h][k], dot);
+                            diff = fmaf(-2.f, dot, Aj + Bh[h]);
+                            band = band_x;
                         } else {
+                            float r2 = 0.f;
                             code = 0u;
 #pragma unroll
                             for (int k = 0; k < D; ++k) {
@@ -179,11 +204,11 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                                 code |= (uint32_t)(o + 1) << (2 * k);
                                 r2 = fmaf(dx, dx, r2);
                             }
+                            const float rc = rh[h] + (dv.rglobal > 0.0 ? dv.hmax_f : rj[D]);
+                            const float rc2 = rc * rc;
+                            diff = r2 - rc2;
+                            band = band_abs + 1e-5f * rc2;
                         }
-                        const float rc = rh[h] + (dv.rglobal > 0.0 ? dv.hmax_f : rj[D]);
-                        const float rc2 = rc * rc;
-                        const float diff = r2 - rc2;
-                        const float band = band_abs + 1e-5f * rc2;
                         if (diff > band) {
                             hit = false;
                         } else if (fabsf(diff) <= band) {
