@@ -106,6 +106,9 @@ struct Dev {
     int32_t *batch_start;   // [ncells+1] exclusive scan of ceil(count / home_batch(d))
     float hmax_f;           // largest radius (sigma_max / 2)
     double rglobal;         // > 0: one list radius sigma_max + s for every pair
+    float rglobal_f;        // the same in FP32: the list build tests it per
+                            // candidate chunk, where an FP64 compare would
+                            // queue on the narrow FP64 pipe
     double *tx, *tv, *tsig, *tim;
     int32_t *timg, *tid;
     // lists

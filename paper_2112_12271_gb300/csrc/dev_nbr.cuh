@@ -7,8 +7,11 @@ namespace hdmd {
 
 // Lists of home batch w (one warp; lane = 0..31).  Called by the grid
 // kernel below (one warp per batch) and by the batched-job kernel (the warps
-// of one block loop over the batches of one job).
-template <int D, bool WRAP>
+// of one block loop over the batches of one job).  ALLH (n_cell >= 3 only):
+// test a candidate against all home atoms branch-free before one vote,
+// instead of one home atom after another; it pays where registers are
+// plentiful enough for more resident warps (d <= 4), not above.
+template <int D, bool WRAP, bool ALLH = false>
 __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
     constexpr int RF = Rows<D>::RF;
     constexpr int H = home_batch(D);
@@ -31,6 +34,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
     }
     const float Lsc = dv.Lsc_f, hLsc = 0.5f * dv.Lsc_f, hL = dv.halfL_f;
     const float skin = (float)dv.skin;
+    const bool glob = dv.rglobal_f > 0.f;   // one list radius for every pair
     const float band_abs = 1e-5f * Lsc * Lsc;
 
     // home atoms in registers (identical in every lane)
@@ -42,7 +46,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
         const float *ri = dv.gs0 + (size_t)i * RF;
 #pragma unroll
         for (int k = 0; k < D; ++k) xh[h][k] = ri[k];
-        rh[h] = (dv.rglobal > 0.0 ? dv.hmax_f : ri[D]) + skin;
+        rh[h] = (glob ? dv.hmax_f : ri[D]) + skin;
         cnt[h] = 0;
     }
     const float reach_pad = dv.hmax_f;   // largest candidate radius
@@ -165,78 +169,131 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
 #pragma unroll
                     for (int k = 0; k < D - 1; ++k) rj[k] += offL[k];
                     rj[D - 1] = fmaf((float)olast, Lsc, rj[D - 1]);
-                    rhoj = dv.rglobal > 0.0 ? dv.hmax_f : rj[D];
+                    rhoj = glob ? dv.hmax_f : rj[D];
                     Aj = -rhoj * rhoj;
 #pragma unroll
                     for (int k = 0; k < D; ++k) Aj = fmaf(rj[k], rj[k], Aj);
                 }
                 const uint32_t wcode = WRAP ? (rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)))) : 0u;
+                if constexpr (WRAP && ALLH) {
+                    // every home atom's test at once (independent chains),
+                    // then one vote: most chunks hold no pair at all
+                    unsigned hits = 0u, close = 0u;
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    if (!(active & (1u << h))) continue;   // warp-uniform
-                    const int i = h0 + h;
-                    bool hit = false;
-                    uint32_t code = wcode;
-                    if (okj && j != i) {
-                        float diff, band;
-                        if (WRAP) {
-                            float dot = rhoj * rh[h];
+                    for (int h = 0; h < H; ++h) {
+                        float da = rhoj * rh[h], db = 0.f;
 #pragma unroll
-                            for (int k = 0; k < D; ++k) dot = fmaf(rj[k], xh[h][k], dot);
-                            diff = fmaf(-2.f, dot, Aj + Bh[h]);
-                            band = band_x;
-                        } else {
-                            float r2 = 0.f;
-                            code = 0u;
+                        for (int k = 0; k < D; ++k) {
+                            if (k & 1) db = fmaf(rj[k], xh[h][k], db);
+                            else da = fmaf(rj[k], xh[h][k], da);
+                        }
+                        const float diff = fmaf(-2.f, da + db, Aj + Bh[h]);
+                        hits |= (diff < -band_x ? 1u : 0u) << h;
+                        close |= (fabsf(diff) <= band_x ? 1u : 0u) << h;
+                    }
+                    const unsigned self = (unsigned)(j - h0) < (unsigned)H ? 1u << (j - h0) : 0u;
+                    const unsigned cand = okj ? (active & ~self) : 0u;
+                    hits &= cand;
+                    close &= cand;
+                    while (close) {   // FP64 decision (positions are x0 at a build)
+                        const int h = __ffs(close) - 1;
+                        close &= close - 1;
+                        const int i = h0 + h;
+                        double s2d = 0.0;
+                        for (int k = 0; k < D; ++k) {
+                            double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
+                            dx -= dv.L * rint(dx * dv.invL);
+                            s2d += dx * dx;
+                        }
+                        const double rcd = glob ? dv.rglobal
+                                                            : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                        if (s2d < rcd * rcd) hits |= 1u << h;
+                    }
+                    if (!__any_sync(0xffffffffu, hits != 0u)) continue;
 #pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                const int ok = k < D - 1 ? (int)((rc0 >> (2 * k)) & 3u) - 1 : olast;   // 0 or +1
-                                float dx = rj[k] - xh[h][k];
-                                int o = ok;
-                                if (ok) {
-                                    const float dp = (rj[k] + Lsc) - xh[h][k];
-                                    if (dp > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
-                                    else dx = dp;
-                                } else if (n == 1) {   // L_sc = L: nearest image either way
-                                    if (dx > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
-                                    else if (dx < -hL) { dx = (rj[k] + Lsc) - xh[h][k]; o = 1; }
+                    for (int h = 0; h < H; ++h) {
+                        if (!(active & (1u << h))) continue;   // warp-uniform
+                        const bool hit = (hits >> h) & 1u;
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (!m) continue;
+                        if (hit) {
+                            const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
+                            if (idx < dv.cap) {
+                                const int64_t pos = list_pos(idx, h0 + h, dv.Npad, dv.lgG);
+                                dv.nbr[pos] = j;
+                                dv.code[pos] = wcode;
+                            }
+                        }
+                        cnt[h] += __popc(m);
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        if (!(active & (1u << h))) continue;   // warp-uniform
+                        const int i = h0 + h;
+                        bool hit = false;
+                        uint32_t code = wcode;
+                        if (okj && j != i) {
+                            float diff, band;
+                            if (WRAP) {
+                                float dot = rhoj * rh[h];
+#pragma unroll
+                                for (int k = 0; k < D; ++k) dot = fmaf(rj[k], xh[h][k], dot);
+                                diff = fmaf(-2.f, dot, Aj + Bh[h]);
+                                band = band_x;
+                            } else {
+                                float r2 = 0.f;
+                                code = 0u;
+#pragma unroll
+                                for (int k = 0; k < D; ++k) {
+                                    const int ok = k < D - 1 ? (int)((rc0 >> (2 * k)) & 3u) - 1 : olast;   // 0 or +1
+                                    float dx = rj[k] - xh[h][k];
+                                    int o = ok;
+                                    if (ok) {
+                                        const float dp = (rj[k] + Lsc) - xh[h][k];
+                                        if (dp > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
+                                        else dx = dp;
+                                    } else if (n == 1) {   // L_sc = L: nearest image either way
+                                        if (dx > hL) { dx = (rj[k] - Lsc) - xh[h][k]; o = -1; }
+                                        else if (dx < -hL) { dx = (rj[k] + Lsc) - xh[h][k]; o = 1; }
+                                    }
+                                    code |= (uint32_t)(o + 1) << (2 * k);
+                                    r2 = fmaf(dx, dx, r2);
                                 }
-                                code |= (uint32_t)(o + 1) << (2 * k);
-                                r2 = fmaf(dx, dx, r2);
+                                const float rc = rh[h] + (glob ? dv.hmax_f : rj[D]);
+                                const float rc2 = rc * rc;
+                                diff = r2 - rc2;
+                                band = band_abs + 1e-5f * rc2;
                             }
-                            const float rc = rh[h] + (dv.rglobal > 0.0 ? dv.hmax_f : rj[D]);
-                            const float rc2 = rc * rc;
-                            diff = r2 - rc2;
-                            band = band_abs + 1e-5f * rc2;
-                        }
-                        if (diff > band) {
-                            hit = false;
-                        } else if (fabsf(diff) <= band) {
-                            // FP64 decision (positions are x0 at a build)
-                            double s2d = 0.0;
-                            for (int k = 0; k < D; ++k) {
-                                double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
-                                dx -= dv.L * rint(dx * dv.invL);
-                                s2d += dx * dx;
+                            if (diff > band) {
+                                hit = false;
+                            } else if (fabsf(diff) <= band) {
+                                // FP64 decision (positions are x0 at a build)
+                                double s2d = 0.0;
+                                for (int k = 0; k < D; ++k) {
+                                    double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
+                                    dx -= dv.L * rint(dx * dv.invL);
+                                    s2d += dx * dx;
+                                }
+                                const double rcd = glob ? dv.rglobal
+                                                                    : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                                hit = s2d < rcd * rcd;
+                            } else {
+                                hit = diff < 0.f;
                             }
-                            const double rcd = dv.rglobal > 0.0 ? dv.rglobal
-                                                                : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
-                            hit = s2d < rcd * rcd;
-                        } else {
-                            hit = diff < 0.f;
                         }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (!m) continue;
-                    if (hit) {
-                        const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
-                        if (idx < dv.cap) {
-                            const int64_t pos = list_pos(idx, i, dv.Npad, dv.lgG);
-                            dv.nbr[pos] = j;
-                            dv.code[pos] = code;
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (!m) continue;
+                        if (hit) {
+                            const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
+                            if (idx < dv.cap) {
+                                const int64_t pos = list_pos(idx, i, dv.Npad, dv.lgG);
+                                dv.nbr[pos] = j;
+                                dv.code[pos] = code;
+                            }
                         }
+                        cnt[h] += __popc(m);
                     }
-                    cnt[h] += __popc(m);
                 }
             }
         }

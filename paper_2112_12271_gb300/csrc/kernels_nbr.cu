@@ -34,15 +34,24 @@ namespace {
 
 constexpr int NT = 128;   // threads per block: 4 warps, one home batch each
 
-template <int D, bool WRAP>
+// resident blocks per SM the register budget is sized for: d <= 4 tests all
+// home atoms of a batch at once in 64 registers at 8 blocks; higher d keeps
+// 80 registers at 6 blocks (more would spill)
 #ifndef HDMD_NBR_MIN_BLOCKS
 #define HDMD_NBR_MIN_BLOCKS 6
 #endif
-__global__ void __launch_bounds__(NT, HDMD_NBR_MIN_BLOCKS) k_nbr_build(Dev dv, bool guarded) {
+#ifndef HDMD_NBR_MIN_BLOCKS_LO
+#define HDMD_NBR_MIN_BLOCKS_LO 8
+#endif
+__host__ __device__ constexpr bool nbr_allh(int D) { return D <= 4; }
+
+template <int D, bool WRAP>
+__global__ void __launch_bounds__(NT, nbr_allh(D) ? HDMD_NBR_MIN_BLOCKS_LO : HDMD_NBR_MIN_BLOCKS)
+k_nbr_build(Dev dv, bool guarded) {
     if (guarded && *((volatile int *)&dv.flags->rebuild) == 0) return;
     const int w = (blockIdx.x * NT + threadIdx.x) >> 5;
     if (w >= dv.batch_start[dv.ncells]) return;   // warp-uniform
-    nbr_batch<D, WRAP>(dv, w, threadIdx.x & 31);
+    nbr_batch<D, WRAP, nbr_allh(D)>(dv, w, threadIdx.x & 31);
 }
 
 template <int D>

@@ -1669,6 +1669,7 @@ hdmd_status set_list_radius(hdmd_system *sys, int global) {
     if (st) return st;
     if (global != 0 && global != 1) return fail(sys, HDMD_E_INVALID, "global must be 0 or 1");
     sys->dv.rglobal = global ? sys->sigma_max + sys->pot.skin : 0.0;
+    sys->dv.rglobal_f = (float)sys->dv.rglobal;
     free_graphs(sys);   // the graphs hold the system description
     return build_forced(sys, sys->buf);
 }
