@@ -98,6 +98,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                 rcode |= (uint32_t)(off[k] + 1) << (2 * k);
             }
             Jrow *= n;
+            unsigned mlo = 0, mhi = 0;   // home atoms reaching the row's lower / upper piece
             if (WRAP) {
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
@@ -109,9 +110,15 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                         b2 = fmaf(dk, dk, b2);
                     }
                     const float reach = (rh[h] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
-                    if (b2 < reach * reach) amask |= 1u << h;
+                    const float r2 = reach * reach;
+                    const float dlo = fmaxf(xh[h][D - 1] + hLsc, 0.f), dhi = fmaxf(hLsc - xh[h][D - 1], 0.f);
+                    if (b2 < r2) amask |= 1u << h;
+                    if (fmaf(dlo, dlo, b2) < r2) mlo |= 1u << h;
+                    if (fmaf(dhi, dhi, b2) < r2) mhi |= 1u << h;
                 }
                 amask &= allh;
+                mlo &= allh;
+                mhi &= allh;
             } else {
                 amask = allh;
             }
@@ -119,10 +126,10 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
             // looked up here for all 32 rows at once (one round trip) rather
             // than row after row in the walk below
             if (amask) {
-                if (WRAP) {
-                    ps1 = dv.cell_start[Jrow + cl_m]; pl1 = dv.cell_start[Jrow + cl_m + 1] - ps1;
+                if (WRAP) {   // a piece no home atom reaches along the last axis either is skipped
+                    ps1 = dv.cell_start[Jrow + cl_m]; pl1 = mlo ? dv.cell_start[Jrow + cl_m + 1] - ps1 : 0;
                     ps2 = dv.cell_start[Jrow + cl];   pl2 = dv.cell_start[Jrow + cl + 1] - ps2;
-                    ps3 = dv.cell_start[Jrow + cl_p]; pl3 = dv.cell_start[Jrow + cl_p + 1] - ps3;
+                    ps3 = dv.cell_start[Jrow + cl_p]; pl3 = mhi ? dv.cell_start[Jrow + cl_p + 1] - ps3 : 0;
                 } else if (n == 2) {
                     ps1 = dv.cell_start[Jrow + cl];     pl1 = dv.cell_start[Jrow + cl + 1] - ps1;
                     ps2 = dv.cell_start[Jrow + 1 - cl]; pl2 = dv.cell_start[Jrow + 2 - cl] - ps2;
