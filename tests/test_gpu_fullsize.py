@@ -9,6 +9,7 @@
 * d = 6, N = 2^21 (the HBM-bound size): sampled atoms' lists and forces
   against the oracle's single-atom definitions, list symmetry and Newton's
   third law over the whole system;
+* the paper's systems at d = 5, 6 (N = 10^5): sampled lists and symmetry;
 * the dimension-sweep systems (N = 65536, d = 4): a FIRE minimum checked by
   the oracle's forces, and one seeded SWAP sweep against the serial oracle.
 
@@ -53,16 +54,16 @@ def c1_ref(c1):
                 md100=oracle.md_steps(s.x, s.v, s.sigma, s.L, 100, 0.005, skin=SKIN))
 
 
-def _is_tie(x, sigma, L, i, j):
+def _is_tie(x, sigma, L, i, j, skin=SKIN):
     dx = x[j] - x[i]
     dx -= L * np.round(dx / L)
     r = float(np.sqrt(dx @ dx))
-    return abs(r - (0.5 * (sigma[i] + sigma[j]) + SKIN)) <= TIE
+    return abs(r - (0.5 * (sigma[i] + sigma[j]) + skin)) <= TIE
 
 
-def _check_row(x, sigma, L, i, gpu_row, ref_row):
+def _check_row(x, sigma, L, i, gpu_row, ref_row, skin=SKIN):
     for j in set(int(a) for a in gpu_row) ^ set(int(b) for b in ref_row):
-        assert _is_tie(x, sigma, L, i, j), (i, j)
+        assert _is_tie(x, sigma, L, i, j, skin), (i, j)
 
 
 def _rows(counts, idx):
@@ -144,6 +145,28 @@ def test_c1_large_sampled_lists_forces_and_symmetry(H):
         _check_row(s.x, s.sigma, s.L, i, rows(i), oracle.neighbors_of(s.x, s.sigma, s.L, SKIN, i))
         Fi, _, _ = oracle.force_on(s.x, s.sigma, s.L, i)
         assert np.abs(F[i] - Fi).max() <= 1e-5 * fmax, i
+
+
+@pytest.mark.parametrize("d", [5, 6])
+def test_paper_model_sampled_lists_and_symmetry(H, d):
+    """The paper's own systems (N = 10^5 at phi*_d, skin 0.25, Sec. III):
+    13 (d = 5) and 24 (d = 6) atoms per subcell, so a stencil row spans
+    several 32-wide chunks and the reach test drops whole subcells along the
+    last axis.  Sampled atoms' lists against the oracle's single-atom search,
+    and list symmetry over the whole system."""
+    skin = 0.25
+    s = W.paper_model(d, 100000, seed=0)
+    N = s.N
+    with H.System(d, s.L, s.sigma, s.x, s.v, skin=skin, precision=H.HDMD_MIXED) as g:
+        counts, idx = g.neighbors()
+    rows = _rows(counts, idx)
+    ii = np.repeat(np.arange(N, dtype=np.int64), counts)
+    jj = idx.astype(np.int64)
+    assert np.array_equal(np.sort(ii * N + jj), np.sort(jj * N + ii))
+    rng = np.random.default_rng(100 + d)
+    for i in rng.choice(N, size=128, replace=False):
+        _check_row(s.x, s.sigma, s.L, i, rows(i),
+                   oracle.neighbors_of(s.x, s.sigma, s.L, skin, i), skin)
 
 
 def test_sweep_d4_fire_minimum_checked_by_oracle(H):
