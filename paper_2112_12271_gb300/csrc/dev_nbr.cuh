@@ -213,7 +213,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                             s2d += dx * dx;
                         }
                         const double rcd = glob ? dv.rglobal
-                                                            : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                                                : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
                         if (s2d < rcd * rcd) hits |= 1u << h;
                     }
                     if (!__any_sync(0xffffffffu, hits != 0u)) continue;
@@ -283,7 +283,7 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                                     s2d += dx * dx;
                                 }
                                 const double rcd = glob ? dv.rglobal
-                                                                    : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                                                        : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
                                 hit = s2d < rcd * rcd;
                             } else {
                                 hit = diff < 0.f;

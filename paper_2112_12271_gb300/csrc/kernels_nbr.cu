@@ -9,17 +9,20 @@
 //     holding many atoms is split over several warps;
 //   - the stencil is walked as 3^(d-1) "rows": the three subcells that differ
 //     only along the last axis are adjacent in the linear index of Eq. (9),
-//     so after the counting sort their atoms form one contiguous range (two
-//     when the row wraps around the box), read with coalesced row loads, one
-//     candidate per lane;
-//   - before a row is read each home atom tests the distance from itself to
-//     the row's box; only home atoms that can reach it test its candidates;
+//     so after the counting sort their atoms lie in up to three ranges, read
+//     with coalesced loads, one candidate per lane;
+//   - 32 rows are set up at once, one per lane (offsets, reach tests, the
+//     ranges), then the warp walks the reachable ones;
+//   - each home atom tests the distance from itself to the row's box and to
+//     the row's lower and upper subcell; only home atoms that can reach the
+//     row test its candidates, and a subcell no home atom reaches is skipped;
 //   - each home atom's hits are compacted with __ballot_sync/__popc, so the
 //     lists come out in the same order on every run;
 //   - a pair is kept iff r^2 < (sigma_ij + s)^2.  The FP32 distance
-//     (cell-relative coordinates, error ~1e-7) decides unless r^2 lies in a
-//     guard band around the cutoff, where the FP64 distance decides, so the
-//     lists equal those of an all-FP64 search.
+//     (cell-relative coordinates, error ~1e-7; for n_cell >= 3 in the
+//     expanded form |r_j|^2 + |x_h|^2 - 2 r_j . x_h, bound in dev_nbr.cuh)
+//     decides unless r^2 lies in a guard band around the cutoff, where the
+//     FP64 distance decides, so the lists equal those of an all-FP64 search.
 // With n_cell = 2 the offsets -1 and +1 name the same subcell, so each
 // subcell is visited once (offsets {0, +1}) and every pair takes the minimum
 // image along the axes where the two subcells differ; the paper switches to
