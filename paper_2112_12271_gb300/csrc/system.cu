@@ -19,6 +19,8 @@
 #include <string>
 #include <tuple>
 #include <type_traits>
+#include <utility>
+#include <utility>
 #include <vector>
 
 #include "../../include/hdmd.h"
@@ -975,28 +977,29 @@ int64_t create_bytes(int d, int64_t N, int64_t ncells, int cap, int G) {
     const size_t RF = kRowFloats(d), RD = kRowDoubles(d);
     const size_t maxblocks = (Np * kMaxLanes + kStepNT - 1) / kStepNT;
     const size_t nc = (size_t)ncells;
-    const Dev *dv = nullptr;
-    const hdmd_system *sy = nullptr;
     int64_t b = 0;
-#define FB(expr, count) b += (int64_t)(sizeof(*(expr)) * ((size_t)(count) ? (size_t)(count) : 1))
-    FB(dv->x0, nd); FB(dv->dlt, nd); FB(dv->v, nd); FB(dv->F, nd);
-    FB(dv->sigma, Np); FB(sy->inv_mass_store, Np); FB(sy->st_f, nd);
-    FB(dv->img, nd); FB(dv->id, Np);
-    FB(dv->gs0, Np * RF); FB(dv->gs[0], Np * RF); FB(dv->gs[1], Np * RF);
-    FB(dv->gd[0], Np * RD); FB(dv->gd[1], Np * RD);
-    FB(dv->cell_count, nc); FB(dv->cell_fill, nc); FB(dv->cell_start, nc + 1);
-    FB(dv->cell_of, Np); FB(dv->perm, Np); FB(dv->cellid, Np); FB(dv->batch_start, nc + 1);
-    FB(dv->tx, nd); FB(dv->tv, nd); FB(dv->tsig, Np); FB(dv->tim, Np);
-    FB(dv->timg, nd); FB(dv->tid, Np);
-    FB(dv->nnbr, Np);
-    FB(dv->partials, (size_t)kNRed * maxblocks);
-    FB(dv->red, kNRed);
-    FB(dv->flags, 1);
-    FB(sy->st_x, nd); FB(sy->st_v, nd); FB(sy->st_m, Np); FB(sy->st_sig, Np);
-    FB(sy->st_i, nd); FB(sy->st_cnt, Np); FB(sy->st_off, Np + 1);
-    FB(sy->snap_x0, nd); FB(sy->snap_dlt, nd); FB(sy->snap_v, nd); FB(sy->snap_sig, Np);
-    FB(sy->snap_im, Np); FB(sy->snap_img, nd); FB(sy->snap_id, Np);
+    auto fb = [&b](size_t elem, size_t count) { b += (int64_t)(elem * (count ? count : 1)); };
+#define FB(m, count) fb(sizeof(*std::declval<Dev &>().m), (size_t)(count))
+#define SB(m, count) fb(sizeof(*std::declval<hdmd_system &>().m), (size_t)(count))
+    FB(x0, nd); FB(dlt, nd); FB(v, nd); FB(F, nd);
+    FB(sigma, Np); SB(inv_mass_store, Np); SB(st_f, nd);
+    FB(img, nd); FB(id, Np);
+    FB(gs0, Np * RF); FB(gs[0], Np * RF); FB(gs[1], Np * RF);
+    FB(gd[0], Np * RD); FB(gd[1], Np * RD);
+    FB(cell_count, nc); FB(cell_fill, nc); FB(cell_start, nc + 1);
+    FB(cell_of, Np); FB(perm, Np); FB(cellid, Np); FB(batch_start, nc + 1);
+    FB(tx, nd); FB(tv, nd); FB(tsig, Np); FB(tim, Np);
+    FB(timg, nd); FB(tid, Np);
+    FB(nnbr, Np);
+    FB(partials, (size_t)kNRed * maxblocks);
+    FB(red, kNRed);
+    FB(flags, 1);
+    SB(st_x, nd); SB(st_v, nd); SB(st_m, Np); SB(st_sig, Np);
+    SB(st_i, nd); SB(st_cnt, Np); SB(st_off, Np + 1);
+    SB(snap_x0, nd); SB(snap_dlt, nd); SB(snap_v, nd); SB(snap_sig, Np);
+    SB(snap_im, Np); SB(snap_img, nd); SB(snap_id, Np);
 #undef FB
+#undef SB
     int64_t c = ((int64_t)(cap + G - 1) / G) * G;
     if (c < G) c = G;
     b += (int64_t)(sizeof(int32_t) + sizeof(uint32_t)) * c * (int64_t)Np;   // nbr, code
