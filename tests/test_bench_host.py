@@ -1,0 +1,45 @@
+"""Host logic of bench.py on the CPU: the clock record taken during the
+timed region (median SM clock and the throttle reasons that reject a run)
+and the measured-peak lookup."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def row(sm, mx=2070, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
+    return "0, %s, %s, 900.5, 0x0000000000000000, %s, %s, %s, %s\n" % (sm, mx, hw, hwt, swt, cap)
+
+
+def test_clean_run():
+    c = bench.ClockSampler.summarize([row(2070), row(2055), row(2070)])
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+
+def test_reasons_are_collected():
+    c = bench.ClockSampler.summarize([row(1800, cap="Active"), row(1500, hwt="Active"),
+                                      row(1600, swt="Active"), row(1700, hw="Active")])
+    assert c["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap",
+                            "sw_thermal_slowdown"]
+    assert c["sm_mhz"] == 1650.0
+
+
+def test_unreadable_rows_are_skipped():
+    lines = ["garbage\n", "0, [N/A], 2070, 1, 0x0, Not Active, Not Active, Not Active, Not Active\n",
+             row(1990)]
+    c = bench.ClockSampler.summarize(lines)
+    assert c["samples"] == 1 and c["sm_mhz"] == 1990.0
+    assert bench.ClockSampler.summarize(["\n"]) is None
+
+
+def test_peaks_reads_measured_file():
+    path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    v, kind = bench.peaks()
+    if os.path.exists(path):
+        with open(path) as f:
+            assert v == pytest.approx(float(json.load(f)["hbm_gbs"]))
+        assert kind == "measured"
+    else:
+        assert (v, kind) == (6800.0, "fallback")
