@@ -43,3 +43,20 @@ def test_peaks_reads_measured_file():
         assert kind == "measured"
     else:
         assert (v, kind) == (6800.0, "fallback")
+
+
+def test_stop_reads_and_removes_the_record(tmp_path):
+    """stop() ends the sampling process, summarises its file and deletes it
+    (a stand-in process and file; no nvidia-smi needed)."""
+    import subprocess
+    import sys
+    path = tmp_path / "clocks.csv"
+    path.write_text(row(2070) + row(2040, cap="Active"))
+    cs = bench.ClockSampler(0)
+    cs.path = str(path)
+    cs.proc = subprocess.Popen([sys.executable, "-c", "import time; time.sleep(30)"])
+    c = cs.stop()
+    assert cs.proc.poll() is not None
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert not path.exists()
+    assert bench.ClockSampler(0).stop() is None          # never started
