@@ -290,6 +290,92 @@ def test_fire_jammed_packing_converges_with_residual_energy(orc):
     assert E == pytest.approx(out["E"], rel=1e-9)
 
 
+def _fire_energies(orc, s, K):
+    """E_pair after k = 0..K iterations, each from its own run capped at k
+    iterations (the paper's stop criteria end a run; they never change its
+    path)."""
+    return np.array([orc.fire(s.x, s.sigma, s.L, max_iter=k)["E"] for k in range(K + 1)])
+
+
+@pytest.mark.parametrize("th", [3e-3, 1e-3])
+def test_fire_fractional_drop_stop_is_first_passage(orc, th):
+    """Sec. II.B, Eq. (6): the run ends at the first iteration that closes ten
+    consecutive fractional energy drops below F_thres."""
+    s = W.make_system(3, 64, phi=0.75, dist="poly", T=0.0, seed=4)
+    r = orc.fire(s.x, s.sigma, s.L, f_thres=th)
+    E = _fire_energies(orc, s, r["iters"])
+    below = np.abs(np.diff(E) / E[:-1]) < th          # drop into iteration k: index k-1
+    first = next((k for k in range(10, len(E)) if below[k - 10:k].all()), None)
+    assert first == r["iters"] and r["status"] == 0
+    assert r["E"] == E[first]
+
+
+@pytest.mark.parametrize("et", [1e-2, 5e-3])
+def test_fire_energy_threshold_stop_is_first_passage(orc, et):
+    """Sec. II.B: the run ends at the first iteration whose energy per atom
+    is below E_thres."""
+    s = W.make_system(3, 64, phi=0.75, dist="poly", T=0.0, seed=4)
+    r = orc.fire(s.x, s.sigma, s.L, e_thres=et)
+    per_atom = _fire_energies(orc, s, r["iters"]) / s.N
+    assert per_atom[-1] < et and (per_atom[:-1] >= et).all()
+    assert r["status"] == 0
+
+
+def test_fire_displacement_cap_two_spheres(orc):
+    """Two unit spheres 0.2 apart: each feels |f| = 1 - 0.2 = 0.8 and starts
+    at rest, so the first FIRE iteration moves each by dt^2 f (here 2e-5)
+    unless Delta_max (Table II) is smaller, when it moves Delta_max."""
+    x = np.array([[0.0, 0.0, 0.0], [0.2, 0.0, 0.0]])
+    sig = np.ones(2)
+    dt = 0.005
+    sep = lambda r: r["x"][1, 0] - r["x"][0, 0]
+    assert sep(orc.fire(x, sig, 10.0, max_iter=1)) == pytest.approx(0.2 + 2 * dt * dt * 0.8, rel=1e-12)
+    assert sep(orc.fire(x, sig, 10.0, max_iter=1, dx_max=1e-5)) == pytest.approx(0.2 + 2e-5, rel=1e-12)
+    assert sep(orc.fire(x, sig, 10.0, max_iter=1, dx_max=1.0)) == pytest.approx(0.2 + 2 * dt * dt * 0.8, rel=1e-12)
+
+
+def test_fire_displacement_cap_bounds_every_iteration(orc):
+    """With Delta_max set no atom moves more than Delta_max per move: at most
+    2 Delta_max per iteration (a back-off and a step), and the cap is reached."""
+    s = W.make_system(3, 64, phi=0.75, dist="poly", T=0.0, seed=4)
+    cap = 0.01
+
+    def steps(**kw):
+        prev, out = s.x, []
+        for k in range(1, 80):
+            xk = orc.fire(s.x, s.sigma, s.L, max_iter=k, **kw)["x"]
+            dx = xk - prev
+            dx -= s.L * np.round(dx / s.L)
+            out.append(np.linalg.norm(dx, axis=1).max())
+            prev = xk
+        return np.array(out)
+
+    free, capped = steps(), steps(dx_max=cap)
+    assert free.max() > 2 * cap                       # the cap matters on this path
+    assert capped.max() <= 2 * cap * (1 + 1e-12)
+    assert (capped >= cap * (1 - 1e-12)).any()
+
+
+def test_fire_displacement_cap_holds_for_the_back_off(orc):
+    """A sphere pushed off its neighbour runs into a third one; there the
+    power turns negative while it moves fast, and FIRE backs off by
+    (dt/2) v.  That move too is capped at Delta_max, so no iteration moves an
+    atom more than 2 Delta_max until the run converges."""
+    x = np.array([[0.0, 0.0, 0.0], [0.3, 0.0, 0.0], [1.6, 0.0, 0.0]])
+    sig = np.ones(3)
+    L, cap = 12.0, 0.002
+    r = orc.fire(x, sig, L, dx_max=cap)
+    assert r["status"] == 0
+    prev, worst = x, 0.0
+    for k in range(1, r["iters"] + 1):
+        xk = orc.fire(x, sig, L, max_iter=k, dx_max=cap)["x"]
+        dx = xk - prev
+        dx -= L * np.round(dx / L)
+        worst = max(worst, np.linalg.norm(dx, axis=1).max())
+        prev = xk
+    assert cap <= worst <= 2 * cap * (1 + 1e-12)
+
+
 # ------------------------------------------------------------------ SWAP
 def test_swap_delta_e_equals_total_energy_change(orc):
     s = W.make_system(3, 120, phi=0.6, dist="bi", T=0.0, seed=9)
