@@ -85,8 +85,10 @@ def test_cells_equal_brute(orc, d, N, L):
         for i, s in enumerate(sets):   # j in VL(i) <=> i in VL(j)
             for j in s:
                 assert i in sets[j]
-    # explicit distance check of a few pairs against the plain definition
+    # explicit distance check of a few pairs against the plain definition,
+    # per-pair radius sigma_ij + s and one global radius sigma_max + s
     sets = orc.lists_as_sets(*orc.neighbors_brute(x, sigma, L, 0.3))
+    gsets = orc.lists_as_sets(*orc.neighbors_brute(x, sigma, L, 0.3, global_cut=True))
     for i in range(0, N, max(1, N // 7)):
         for j in range(N):
             if j == i:
@@ -95,6 +97,24 @@ def test_cells_equal_brute(orc, d, N, L):
             dx -= L * np.round(dx / L)
             inside = float(dx @ dx) < (0.5 * (sigma[i] + sigma[j]) + 0.3) ** 2
             assert inside == (j in sets[i])
+            assert (float(dx @ dx) < (sigma.max() + 0.3) ** 2) == (j in gsets[i])
+
+
+def test_cells_with_atoms_on_the_box_faces(orc):
+    """Coordinates at -L/2 and at the last value below +L/2 lie in the first
+    and the last subcell (Eq. (8)); the subcell search still equals brute
+    force."""
+    d, N, L = 3, 300, 7.0
+    x, sigma = _random_system(d, N, L, seed=11)
+    top = np.nextafter(0.5 * L, 0.0)
+    x[:40, 0] = top
+    x[40:80, 1] = -0.5 * L
+    x[80:100, 2] = top
+    x[100:110] = top
+    for gc in (False, True):
+        cb, ib = orc.neighbors_brute(x, sigma, L, 0.3, global_cut=gc)
+        cc, ic = orc.neighbors_cells(x, sigma, L, 0.3, global_cut=gc)
+        assert (cb == cc).all() and (ib == ic).all()
 
 
 @pytest.mark.parametrize("row", read_golden("lattice_neighbor_counts.txt")[:6])
@@ -665,11 +685,12 @@ def test_mie_closed_forms_and_gradient(orc, n):
         assert fd == pytest.approx(orc.mie(r, s, eps, n)[1] * r, rel=1e-6)
 
 
-def test_berendsen_barostat_ideal_gas_volume_relaxes_geometrically(orc):
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_berendsen_barostat_ideal_gas_volume_relaxes_geometrically(orc, d):
     """No forces: P_n = N T / V_n with T fixed, and mu^d = 1 - c (P_t - P_n),
     c = beta n_baro dt / tau_P, so V_{n+1} - V* = (1 - c P_t)(V_n - V*) with
     V* = N T / P_t."""
-    x, v, sigma, L = _ideal_gas(d=3, N=400, seed=7)
+    x, v, sigma, L = _ideal_gas(d=d, N=400, seed=7)
     N, d = x.shape
     T = 2 * orc.kinetic(v) / (d * (N - 1))
     Pt, tau_P, beta, nb, dt = 2.5, 0.5, 0.3, 10, 0.004
@@ -693,3 +714,85 @@ def test_paper_rebuild_rule_counts_and_misses(orc):
     assert 1 <= pp["builds"] <= ex["builds"]
     Fb, _, _ = orc.forces(ex["x"], s.sigma, s.L)
     assert np.abs(ex["F"] - Fb).max() < 1e-12 * np.abs(Fb).max()
+
+
+@pytest.mark.parametrize("movers,period", [(1, 28), (2, 14)])
+def test_paper_rule_thresholds(orc, movers, period):
+    """Sec. II.C: rebuild when at least 0.1 % of the atoms have moved s/2 or
+    more since the last build, or any atom s or more.  Of 2000 atoms at rest
+    (too small to touch), `movers` fly 0.011 per step: one mover (0.05 %)
+    triggers a build each time it has flown s = 0.3 (every 28 steps), two
+    (0.1 %) each time they have flown s/2 (every 14 steps).  Checked every
+    step (n_bet = 1), over 200 steps, plus the initial build."""
+    d, N, L = 2, 2000, 60.0
+    x, _ = W.lattice(d, 45, 60.0 / 45)
+    x = x[:N].copy()
+    v = np.zeros((N, d))
+    v[:movers, 0] = 1.1
+    x[:movers, 1] += 0.5              # off the lattice rows they fly along
+    sigma = np.full(N, 1e-3)
+    r = orc.md_steps(x, v, sigma, L, 200, 0.01, skin=0.3, rule="paper", n_bet=1)
+    assert r["builds"] == 1 + 200 // period
+
+
+def test_image_counts_unwrap_free_flight(orc):
+    """Atoms that never touch fly straight: x + L img equals x0 + v t after
+    several crossings of both faces of the box."""
+    d, L = 3, 6.0
+    x = np.array([[0.1, -2.9, 2.0], [-1.0, 1.0, -2.5], [2.5, 0.3, 0.0],
+                  [-2.2, -1.4, 1.1], [1.3, 2.6, -0.7], [0.0, 0.0, 0.0]])
+    v = np.array([[2.3, -1.7, 0.4], [-3.1, 0.2, 1.9], [0.7, 2.8, -2.6],
+                  [1.5, -0.9, -3.3], [-0.6, 3.4, 0.8], [2.9, 2.1, -1.2]])
+    sigma = np.full(len(x), 1e-3)
+    r = orc.md_steps(x, v, sigma, L, 1000, 0.01, skin=2.0)
+    assert np.abs(r["x"] + L * r["img"] - (x + 10.0 * v)).max() < 1e-9
+    assert r["img"].max() >= 3 and r["img"].min() <= -3
+    assert np.all(r["x"] >= -0.5 * L) and np.all(r["x"] < 0.5 * L)
+
+
+def test_fire_mixing_and_schedule_seen_from_the_trajectory(orc):
+    """FIRE 2.0 (Guenole et al. 2020) observed from outside, from the states
+    after k and k + 1 iterations (capped runs).  An iteration with
+    P = F.v > 0 moves x by dt v_{k+1} with v_{k+1} = (1 - alpha) v' +
+    alpha |v'| F/|F|, v' = v_k + dt F_k (norms over all atoms); one with
+    P <= 0 restarts from rest (v_{k+1} = dt F_k).  The dt so measured never
+    exceeds dt_max and reaches it; a P <= 0 step past the initial delay
+    multiplies dt by f_dec and sets alpha back to alpha0 (it had decayed).
+    The scene: a sphere pushed off its neighbour runs into a third (the
+    P <= 0 step), while a separate pair far away keeps F and v apart so that
+    alpha is measurable."""
+    x = np.array([[0.0, 0.0, 0.0], [0.3, 0.05, 0.0], [1.6, 0.0, 0.0],
+                  [-4.0, 0.0, 0.0], [-4.0, 0.9, 0.0]])
+    sig = np.ones(5)
+    L, dt_max, f_dec, alpha0, n_delay = 12.0, 0.02, 0.5, 0.25, 20
+    K = 110
+    runs = [orc.fire(x, sig, L, max_iter=k, dt_max=dt_max) for k in range(K + 2)]
+    dts, alphas, events = {}, {}, []
+    for k in range(1, K + 1):
+        a, b = runs[k], runs[k + 1]
+        P = float((a["F"] * a["v"]).sum())
+        v1 = b["v"]
+        if P > 0:
+            dx = b["x"] - a["x"]
+            dx -= L * np.round(dx / L)
+            dt = float((dx * v1).sum() / (v1 * v1).sum())
+            assert np.abs(dx - dt * v1).max() <= 1e-12 * np.abs(v1).max() * dt + 1e-15
+            vp = a["v"] + dt * a["F"]
+            u = np.linalg.norm(vp) * a["F"] / np.linalg.norm(a["F"]) - vp
+            if np.linalg.norm(u) > 1e-2 * np.linalg.norm(vp):     # alpha well defined
+                al = float(((v1 - vp) * u).sum() / (u * u).sum())
+                assert np.abs(v1 - (vp + al * u)).max() <= 1e-9 * np.abs(v1).max()
+                alphas[k] = al
+        else:
+            dt = float(np.linalg.norm(v1) / np.linalg.norm(a["F"]))
+            assert np.abs(v1 - dt * a["F"]).max() <= 1e-12 * np.abs(v1).max()
+            events.append(k)
+        dts[k] = dt
+    assert max(dts.values()) <= dt_max * (1 + 1e-9)
+    assert max(dts.values()) >= dt_max * (1 - 1e-9)
+    late = [k for k in events if k > n_delay]
+    assert late, events
+    j = late[0]
+    assert dts[j] == pytest.approx(f_dec * dts[j - 1], rel=1e-9)
+    assert alphas[j + 1] == pytest.approx(alpha0, rel=1e-6)
+    assert alphas[j - 1] < 0.8 * alpha0
