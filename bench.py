@@ -50,6 +50,27 @@ def dist_env():
     return ws, rank, local
 
 
+def l2_bytes():
+    """The device's L2 size in bytes; None where this PyTorch does not expose
+    it or there is no device."""
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size)
+    except Exception:
+        return None
+
+
+def footprint_bytes(s):
+    """Device bytes of the system as the library allocates them (lists at
+    their initial capacity): set against the L2 size it says whether the
+    timed kernel streams from HBM or runs out of L2."""
+    try:
+        from paper_2112_12271_gb300 import hdmd
+        return int(hdmd.system_footprint(s.d, s.N, s.L, s.sigma))
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -311,7 +332,8 @@ def run_gpu(args):
                      "frac": achieved / peak if achieved else None,
                      "traffic": TRAFFIC.get(args.workload),
                      "kernel": "k_step<6,mixed> (pair forces + kicks + drift)",
-                     "bytes_per_atom": bytes_per_atom, "peak_kind": peak_kind},
+                     "bytes_per_atom": bytes_per_atom, "peak_kind": peak_kind,
+                     "l2_bytes": l2_bytes(), "footprint_bytes": footprint_bytes(s)},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * s.N * d * 8,
                 "d2h_bytes_per_step": 7 * 8},

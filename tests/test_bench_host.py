@@ -60,3 +60,15 @@ def test_stop_reads_and_removes_the_record(tmp_path):
     assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
     assert not path.exists()
     assert bench.ClockSampler(0).stop() is None          # never started
+
+
+def test_l2_and_footprint_fields():
+    """The roofline record sets the system's device footprint against the L2
+    size: the d=6, N=32768 benchmark system fits in GB300's 129 MB L2 (the
+    fused step runs out of L2), the N=2^21 one does not."""
+    from paper_2112_12271_gb300 import workloads as W
+    l2 = bench.l2_bytes()
+    assert l2 is None or l2 > 0
+    small = bench.footprint_bytes(W.c1_poly_d6(0))
+    large = bench.footprint_bytes(W.c1_poly_d6(0, N=2 ** 21))
+    assert small < 129e6 < large
