@@ -29,6 +29,8 @@ class Tracker:
         self.running = 0
         self.peak = 0
         self.started = []        # N of each system job, in start order
+        self.start_time = {}     # N -> perf_counter at start
+        self.running_at_start = []
         self.batch_added = []    # N of each batched job, in admission order
         self.batch_peak = 0
 
@@ -48,6 +50,8 @@ def fakes(tracker, batch_capacity=64):
                 tracker.running += 1
                 tracker.peak = max(tracker.peak, tracker.running)
                 tracker.started.append(self.N)
+                tracker.start_time[self.N] = time.perf_counter()
+                tracker.running_at_start.append(tracker.running)
             return self
 
         def __exit__(self, *exc):
@@ -138,18 +142,18 @@ def server(**kw):
 
 def test_small_jobs_batched_big_jobs_on_systems(patched):
     tr = patched()
-    Ns = [50, 2000, 60, 3000, 70, 4000]
-    reqs, systems = jobs(Ns, kinds=[0, 1, 1, 0, 0, 1])
+    Ns = [50, 2000, 60, 3000, 100, 4000, 101]          # 100 = small_N joins the batch
+    reqs, systems = jobs(Ns, kinds=[0, 1, 1, 0, 0, 1, 0])
     srv = server()
-    recs = srv.run(reqs, systems)
+    recs = srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     assert all(r.done is not None for r in recs)
     for r in recs:
         assert r.path == ("batch" if r.req["N"] <= 100 else "system")
         assert r.status == hdmd.JOB_DONE
         assert r.admitted >= r.arrival - 1e-9 and r.done >= r.admitted
-    assert sorted(tr.started) == [2000, 3000, 4000]
-    assert sorted(tr.batch_added) == [50, 60, 70]
+    assert sorted(tr.started) == [101, 2000, 3000, 4000]
+    assert sorted(tr.batch_added) == [50, 60, 100]
     # MD results carry the stand-in energy of their own job
     for r in recs:
         if r.path == "system" and r.req["kind"] == hdmd.JOB_MD:
@@ -162,17 +166,19 @@ def test_device_memory_bounds_concurrent_systems(patched):
     reqs, systems = jobs(Ns)
     # room for two of these footprints at once, not three
     srv = server(slots=8, mem_bytes=int(2.5 * FOOT * 1000))
-    recs = srv.run(reqs, systems)
+    recs = srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     assert all(r.done is not None for r in recs)
     assert tr.peak == 2
+    # finished jobs return their reservation: later jobs run in pairs again
+    assert tr.running_at_start.count(2) >= 2, tr.running_at_start
 
 
 def test_job_larger_than_memory_runs_alone(patched):
     tr = patched()
     reqs, systems = jobs([5000, 1001, 1002])
     srv = server(slots=8, mem_bytes=FOOT * 3000)   # the first job alone exceeds it
-    recs = srv.run(reqs, systems)
+    recs = srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     assert all(r.done is not None for r in recs)
     assert tr.started[0] == 5000
@@ -185,10 +191,13 @@ def test_slot_limit(patched):
     tr = patched()
     reqs, systems = jobs([1000 + k for k in range(9)])
     srv = server(slots=3)
-    recs = srv.run(reqs, systems)
+    recs = srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     assert all(r.done is not None for r in recs)
     assert tr.peak == 3
+    # no job is admitted beyond the slots to wait for a worker
+    for r in recs:
+        assert tr.start_time[r.req["N"]] - (srv._t0 + r.admitted) < 0.5 * JOB_S
 
 
 @pytest.mark.parametrize("policy", ["fifo", "sjf"])
@@ -198,7 +207,7 @@ def test_admission_order(patched, policy):
     nsteps = [100, 400, 50, 100, 100]          # work N * nsteps: 4e5 6e5 1.5e5 1.2e5 2.5e5
     reqs, systems = jobs(Ns, nsteps=nsteps)
     srv = server(slots=1, policy=policy)
-    srv.run(reqs, systems)
+    srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     if policy == "fifo":
         assert tr.started == Ns
@@ -211,7 +220,7 @@ def test_fifo_keeps_arrival_order_over_time(patched):
     Ns = [1500, 1200, 1800, 1100]
     reqs, systems = jobs(Ns, t=[0.03, 0.0, 0.02, 0.01])
     srv = server(slots=1)
-    recs = srv.run(reqs, systems)
+    recs = srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     assert tr.started == [1200, 1100, 1800, 1500]
     for r in recs:
@@ -223,7 +232,7 @@ def test_full_batch_pool_holds_jobs_back(patched):
     Ns = [10 + k for k in range(7)]
     reqs, systems = jobs(Ns, nsteps=[200] * 7)
     srv = server(budget=50)
-    recs = srv.run(reqs, systems)
+    recs = srv.run(reqs, systems, time_limit=20.0)
     srv.close()
     assert all(r.done is not None and r.path == "batch" for r in recs)
     assert tr.batch_peak == 2
