@@ -78,3 +78,45 @@ def test_footprint_needs_no_gpu(libpath):
     assert 0 < small < big
     with pytest.raises(hdmd.HDMDError):
         hdmd.system_footprint(3, 10, 2.0, np.ones(10))      # box too small
+
+
+@pytest.mark.parametrize("case", [
+    dict(d=1), dict(d=11), dict(N=1), dict(L=0.0), dict(L=float("inf")),
+    dict(L=float("nan")), dict(diam_nan=True), dict(diam_zero=True), dict(eps=0.0),
+    dict(skin=-0.1), dict(skin=float("nan")), dict(law="morse", a=0.0),
+    dict(law="mie", n=0), dict(law="mie", n=25), dict(precision=7), dict(L=2.0),
+])
+def test_every_argument_rule_is_checked_without_a_gpu(libpath, case):
+    """Each argument rule of create_system (same checks as system_footprint)
+    answers HDMD_E_INVALID or HDMD_E_UNSUPPORTED_D with a message, before any
+    device work."""
+    from paper_2112_12271_gb300 import hdmd
+    import numpy as np
+    c = dict(d=3, N=10, L=9.0, eps=1.0, skin=0.3, precision=hdmd.HDMD_MIXED,
+             law="harmonic", a=30.0, n=6)
+    c.update(case)
+    diam = np.ones(max(c["N"], 1))[: c["N"]]
+    if c.pop("diam_nan", False):
+        diam[2] = float("nan")
+    if c.pop("diam_zero", False):
+        diam[5] = 0.0
+    with pytest.raises(hdmd.HDMDError) as e:
+        hdmd.system_footprint(c["d"], c["N"], c["L"], diam, eps=c["eps"], skin=c["skin"],
+                              precision=c["precision"], law=c["law"], a=c["a"], n=c["n"])
+    assert e.value.status in (1, 8)
+    assert len(str(e.value)) > 10
+
+
+def test_footprint_grows_with_the_system(libpath):
+    """Footprint: linear growth with N at a fixed density, FP64 systems no
+    smaller than mixed ones, and the laws change no array sizes."""
+    from paper_2112_12271_gb300 import hdmd
+    import numpy as np
+    base = [hdmd.system_footprint(4, N, 6.0 * (N / 4096) ** 0.25, np.ones(N)) for N in (4096, 8192, 16384)]
+    assert base[0] < base[1] < base[2]
+    assert 1.6 < base[2] / base[1] < 2.4
+    s = np.ones(4096)
+    mixed = hdmd.system_footprint(4, 4096, 6.0, s, precision=hdmd.HDMD_MIXED)
+    fp64 = hdmd.system_footprint(4, 4096, 6.0, s, precision=hdmd.HDMD_FP64)
+    assert fp64 >= mixed
+    assert hdmd.system_footprint(4, 4096, 6.0, s, law="morse") == mixed
