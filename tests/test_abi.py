@@ -120,3 +120,28 @@ def test_footprint_grows_with_the_system(libpath):
     fp64 = hdmd.system_footprint(4, 4096, 6.0, s, precision=hdmd.HDMD_FP64)
     assert fp64 >= mixed
     assert hdmd.system_footprint(4, 4096, 6.0, s, law="morse") == mixed
+
+
+@pytest.mark.parametrize("args,status,text", [
+    ((1, 100, 5.0, 1.0), 8, b"d must be"),
+    ((11, 100, 5.0, 1.0), 8, b"d must be"),
+    ((3, 1, 5.0, 1.0), 1, b"N must be"),
+    ((3, 524289, 5.0, 1.0), 1, b"scratch limit"),
+    ((3, 100, 0.0, 1.0), 1, b"positive and finite"),
+    ((3, 100, 5.0, -1.0), 1, b"positive and finite"),
+    ((3, 100, 5.0, 1.0), 1, b"NULL buffer"),
+])
+def test_noalloc_arguments_checked_before_device_work(libpath, args, status, text):
+    """The allocation-free force call rejects bad sizes, its scratch limit
+    (524,288 atoms) and missing buffers before it touches the device (NULL
+    buffers here, so nothing could be launched)."""
+    lib = ctypes.CDLL(libpath)
+    f = lib.compute_forces_noalloc
+    f.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    lib.hdmd_noalloc_last_error.restype = ctypes.c_char_p
+    d, N, L, eps = args
+    assert f(d, N, L, None, None, eps, None, None, None) == status
+    assert text in lib.hdmd_noalloc_last_error()
