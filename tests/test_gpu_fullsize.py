@@ -9,7 +9,7 @@
 * d = 6, N = 2^21 (the HBM-bound size): sampled atoms' lists and forces
   against the oracle's single-atom definitions, list symmetry and Newton's
   third law over the whole system;
-* the paper's systems at d = 5, 6 (N = 10^5): sampled lists and symmetry;
+* the paper's systems at d = 3..6 (N = 10^5): sampled lists and symmetry;
 * the dimension-sweep systems (N = 65536, d = 4): a FIRE minimum checked by
   the oracle's forces, and one seeded SWAP sweep against the serial oracle.
 
@@ -147,13 +147,14 @@ def test_c1_large_sampled_lists_forces_and_symmetry(H):
         assert np.abs(F[i] - Fi).max() <= 1e-5 * fmax, i
 
 
-@pytest.mark.parametrize("d", [5, 6])
+@pytest.mark.parametrize("d", [3, 4, 5, 6])
 def test_paper_model_sampled_lists_and_symmetry(H, d):
     """The paper's own systems (N = 10^5 at phi*_d, skin 0.25, Sec. III):
     13 (d = 5) and 24 (d = 6) atoms per subcell, so a stencil row spans
     several 32-wide chunks and the reach test drops whole subcells along the
-    last axis.  Sampled atoms' lists against the oracle's single-atom search,
-    and list symmetry over the whole system."""
+    last axis; at d = 3, 4 (4 and 7 atoms per subcell) the build tests every
+    home atom of a batch at once.  Sampled atoms' lists against the oracle's
+    single-atom search, and list symmetry over the whole system."""
     skin = 0.25
     s = W.paper_model(d, 100000, seed=0)
     N = s.N
