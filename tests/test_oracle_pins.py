@@ -790,9 +790,110 @@ def test_fire_mixing_and_schedule_seen_from_the_trajectory(orc):
         dts[k] = dt
     assert max(dts.values()) <= dt_max * (1 + 1e-9)
     assert max(dts.values()) >= dt_max * (1 - 1e-9)
+    # dt grows only after N_delay = 20 steps with P > 0 (iteration 0 starts
+    # from rest, P = 0): dt0 through iteration 20, dt0 f_inc at 21
+    assert all(dts[k] == pytest.approx(0.005, rel=1e-9) for k in range(1, n_delay + 1))
+    assert dts[n_delay + 1] == pytest.approx(0.005 * 1.1, rel=1e-9)
     late = [k for k in events if k > n_delay]
     assert late, events
     j = late[0]
     assert dts[j] == pytest.approx(f_dec * dts[j - 1], rel=1e-9)
     assert alphas[j + 1] == pytest.approx(alpha0, rel=1e-6)
     assert alphas[j - 1] < 0.8 * alpha0
+
+
+def _collision_scene():
+    x = np.array([[0.0, 0.0, 0.0], [0.3, 0.05, 0.0], [1.6, 0.0, 0.0],
+                  [-4.0, 0.0, 0.0], [-4.0, 0.9, 0.0]])
+    return x, np.ones(5), 12.0
+
+
+def test_fire_dt_floor_at_the_negative_power_step(orc):
+    """On P <= 0 past the initial delay dt = max(f_dec dt, dt_min): with
+    dt_min above f_dec dt_max the step after the collision uses dt_min (the
+    velocity restarts from rest, v = dt F)."""
+    x, sig, L = _collision_scene()
+    kw = dict(dt_max=0.02, dt_min=0.015)
+    prev = None
+    for k in range(1, 200):
+        a = orc.fire(x, sig, L, max_iter=k, **kw)
+        if k > 20 and float((a["F"] * a["v"]).sum()) <= 0:
+            b = orc.fire(x, sig, L, max_iter=k + 1, **kw)
+            dt = np.linalg.norm(b["v"]) / np.linalg.norm(a["F"])
+            assert dt == pytest.approx(0.015, rel=1e-9)
+            assert np.abs(b["v"] - dt * a["F"]).max() <= 1e-12 * np.abs(b["v"]).max()
+            return
+    pytest.fail("no P <= 0 step")
+
+
+def test_fire_negative_step_counter_counts_consecutive_steps(orc):
+    """N_neg,max bounds consecutive P <= 0 steps: the start from rest
+    (P = 0) and the collision are separated by P > 0 steps, so even
+    n_neg_max = 1 lets the run converge as with the default."""
+    x, sig, L = _collision_scene()
+    ref = orc.fire(x, sig, L)
+    r = orc.fire(x, sig, L, n_neg_max=1)
+    assert ref["status"] == 0 and r["status"] == 0 and r["iters"] == ref["iters"]
+
+
+def test_barostat_count_carries_across_calls(orc):
+    """The barostat acts every n_baro steps counted across calls: 15 + 15
+    steps rescale at steps 10, 20 and 30 like one call of 30."""
+    x, v, sigma, L = _ideal_gas(d=3, N=400, seed=7)
+    args = (2.5, 0.5, 0.3, 10)
+    one = orc.md_npt(x, v, sigma, L, 30, 0.004, *args, skin=2.0)
+    a = orc.md_npt(x, v, sigma, L, 15, 0.004, *args, skin=2.0)
+    b = orc.md_npt(a["x"], a["v"], sigma, a["L"], 15, 0.004, *args, skin=2.0, img=a["img"],
+                   count=a["count"])
+    assert one["rescales"] == 3 and a["rescales"] == 1 and b["rescales"] == 2
+    assert a["count"] == 5 and b["count"] == 0
+    assert b["L"] == pytest.approx(one["L"], rel=1e-12)
+
+
+@pytest.mark.parametrize("nsteps,builds", [(15, 1), (16, 2)])
+def test_paper_rule_checked_at_multiples_of_n_bet(orc, nsteps, builds):
+    """With n_bet = 4 the paper's rule is evaluated after steps 4, 8, 12,
+    16, ...: two movers pass s/2 during step 14, so the rebuild comes at step
+    16, not before."""
+    d, N, L = 2, 2000, 60.0
+    x, _ = W.lattice(d, 45, 60.0 / 45)
+    x = x[:N].copy()
+    v = np.zeros((N, d))
+    v[:2, 0] = 1.1
+    x[:2, 1] += 0.5
+    r = orc.md_steps(x, v, np.full(N, 1e-3), L, nsteps, 0.01, skin=0.3, rule="paper", n_bet=4)
+    assert r["builds"] == builds
+
+
+def test_swap_draw_is_a_scaled_uniform(orc):
+    """Each candidate index is one uniform variate scaled to its range:
+    i = floor(U N) and j' = floor(U' (N - 1)) with U, U' fixed by seed, pass
+    and pair, so i(N)/N (and j'(N)/(N - 1)) agree across N to within 1/N."""
+    big = 1 << 26
+    Ns = [2, 3, 7, 10, 97, 1000, 4093, 65536]
+    pairs_big, _ = orc.swap_draw(2024, 5, 16, big)
+    for p in range(16):
+        i_big = int(pairs_big[p, 0])
+        U_lo, U_hi = i_big / big, (i_big + 1) / big
+        for N in Ns:
+            pr, _ = orc.swap_draw(2024, 5, 16, N)
+            i, j = int(pr[p, 0]), int(pr[p, 1])
+            assert math.floor(U_lo * N) <= i <= math.floor(U_hi * N - 1e-12)
+            assert 0 <= j < N and j != i
+    # j' = j - (j > i), over N - 1 values
+    for p in range(16):
+        i_b, j_b = (int(t) for t in pairs_big[p])
+        jp_big = j_b - (j_b > i_b)
+        V_lo, V_hi = jp_big / (big - 1), (jp_big + 1) / (big - 1)
+        for N in Ns[1:]:
+            pr, _ = orc.swap_draw(2024, 5, 16, N)
+            i, j = int(pr[p, 0]), int(pr[p, 1])
+            jp = j - (j > i)
+            assert math.floor(V_lo * (N - 1)) <= jp <= math.floor(V_hi * (N - 1) - 1e-12)
+
+
+def test_kinetic_energy_with_masses(orc):
+    v = np.array([[1.0, 0.0], [0.0, 2.0], [3.0, -1.0]])
+    m = np.array([2.0, 3.0, 0.5])
+    assert orc.kinetic(v, m) == pytest.approx(0.5 * (2 * 1 + 3 * 4 + 0.5 * 10), rel=1e-15)
+    assert orc.kinetic(v) == pytest.approx(0.5 * (1 + 4 + 10), rel=1e-15)
