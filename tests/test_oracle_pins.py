@@ -897,3 +897,20 @@ def test_kinetic_energy_with_masses(orc):
     m = np.array([2.0, 3.0, 0.5])
     assert orc.kinetic(v, m) == pytest.approx(0.5 * (2 * 1 + 3 * 4 + 0.5 * 10), rel=1e-15)
     assert orc.kinetic(v) == pytest.approx(0.5 * (1 + 4 + 10), rel=1e-15)
+
+
+def test_thermo_describes_the_returned_state(orc):
+    """E and W returned by a run describe the state it returns, also after
+    zero steps and when the run ends on a barostat rescaling: the brute-force
+    all-pairs forces at the returned positions and box give the same E, W."""
+    s = W.make_system(3, 300, phi=0.5, dist="poly", T=0.05, seed=12)
+    r0 = orc.md_steps(s.x, s.v, s.sigma, s.L, 0, 0.005)
+    F, E, Wv = orc.forces(s.x, s.sigma, s.L)
+    assert r0["E"] == pytest.approx(E, rel=1e-12) and r0["W"] == pytest.approx(Wv, rel=1e-12)
+    assert np.abs(r0["F"] - F).max() <= 1e-12 * np.abs(F).max()
+    r0f = orc.md_steps(s.x, s.v, s.sigma, s.L, 0, 0.005, F=F)      # forces handed in
+    assert r0f["E"] == pytest.approx(E, rel=1e-12) and r0f["W"] == pytest.approx(Wv, rel=1e-12)
+    r = orc.md_npt(s.x, s.v, s.sigma, s.L, 20, 0.005, 1.0, 0.5, 0.3, 10)
+    assert r["rescales"] == 2 and r["count"] == 0
+    _, E1, W1 = orc.forces(r["x"], s.sigma, r["L"])
+    assert r["E"] == pytest.approx(E1, rel=1e-12) and r["W"] == pytest.approx(W1, rel=1e-12)
