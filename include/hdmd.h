@@ -256,7 +256,12 @@ hdmd_status observables(hdmd_system *sys, double a_ov, int nbins, double r_max,
  * returns to NVE.  T_target must be >= 0 and finite (HDMD_E_INVALID). */
 hdmd_status set_thermostat(hdmd_system *sys, double T_target, double tau);
 
-/* FIRE 2.0 minimisation (Sec. II.B).  params NULL takes the defaults
+/* FIRE 2.0 minimisation (Sec. II.B names the method; the steps are those
+ * of the published FIRE 2.0 algorithm, Guenole et al. 2020: on P = F.v <= 0
+ * past the initial delay dt *= f_dec only while f_dec dt >= dt_min, and
+ * alpha = alpha0; x -= dt v/2, v = 0; then in every iteration v += dt F/m,
+ * v = (1 - alpha) v + alpha |v| F/|F| over all atoms, x += dt v).
+ * params NULL takes the defaults
  * (dt0 0.005, dt_max 0.05, dt_min 1e-4, f_inc 1.1, f_dec 0.5, alpha0 0.25,
  * f_alpha 0.99, f_tol 1e-10, polish_tol 1e-6, n_delay 20, n_neg_max 2000,
  * max_iter 10^6, initial_delay 1).  Velocities are zeroed on entry and the
@@ -295,14 +300,23 @@ hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs);
 hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_out);
 
 /* Forces, pair energy and virial of N harmonic spheres, for callers that
- * cannot allocate GPU memory when they need them: code running while a CUDA
- * graph is captured (allocation cannot be captured), plug-ins inside a host
- * framework whose memory pool owns the device, loops that forbid allocation
- * after start-up.  The paper has no counterpart of this call; it is the FP64
- * force kernel with all pairs in place of the Verlet list, so it needs no
- * system handle, no list and no cell arrays.
- * Arguments: d in 2..10; N atoms, at most 524288; box side L (which must be
- * at least twice the largest diameter, not checked); device pointers x_dev
+ * cannot allocate GPU memory when they need them: plug-ins inside a host
+ * framework whose memory pool owns the device (a cudaMalloc of their own
+ * would bypass, or fail under, that pool's budget), and loops that forbid
+ * allocation after start-up (an allocation can block on the whole device
+ * and its time is unbounded).  The paper has no counterpart of this call; it
+ * is the FP64 force kernel with all pairs in place of the Verlet list, so it
+ * needs no system handle, no list and no cell arrays.
+ * Cost: all N^2 pairs in FP64, O(N^2 d) work, which the narrow FP64 pipe of
+ * this GPU makes the bound; it suits small and mid-size systems, not the
+ * largest N it accepts.  Measured on one GB300: 12 ms per call at d = 3,
+ * N = 16384; 22 ms at d = 6, N = 16384; 0.32 s at d = 6, N = 65536 (so
+ * about 80 s at the 524288-atom limit).
+ * Arguments: d in 2..10; N atoms, 2 to 524288; box side L, which must be at
+ * least twice the largest diameter (not checked: the kernel evaluates the
+ * nearest image of each pair, which is then the only image that can
+ * overlap; in a smaller box a pair can also overlap through a farther image,
+ * which is left out); device pointers x_dev
  * [N*d] row-major positions, sigma_dev [N] diameters, F_dev [N*d] forces out,
  * ew_dev [2] out (pair energy, virial); eps as in hdmd_potential; cuda_stream
  * a cudaStream_t (NULL = legacy default stream).  The call is asynchronous:
@@ -310,11 +324,11 @@ hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_ou
  * Memory: it allocates nothing.  Its only scratch is a file-scope device
  * array of 65,792 bytes that every GPU loading the library holds until the
  * process exits.  The first call on a device looks up that array's device
- * address (once per device, with the device current), so make the first
- * call before any stream capture.  All calls share the array and it keeps
- * the last call's contents (the call clears what must start at zero), so
- * calls that overlap on the GPU, on any streams, race: serialise them.
- * Errors: HDMD_E_UNSUPPORTED_D, HDMD_E_INVALID (N above the limit, NULL
+ * address (once per device, with the device current).  All calls share the
+ * array and it keeps the last call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU, on any streams, race:
+ * serialise them.
+ * Errors: HDMD_E_UNSUPPORTED_D, HDMD_E_INVALID (N out of range, NULL
  * buffer, bad L or eps), HDMD_E_CUDA; hdmd_noalloc_last_error() gives the
  * reason. */
 hdmd_status compute_forces_noalloc(int d, int64_t N, double L, const double *x_dev,

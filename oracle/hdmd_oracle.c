@@ -626,10 +626,13 @@ typedef struct {
  *   - P = F.v over all atoms; on P > 0: Npos += 1, Nneg = 0, and after
  *     n_delay such steps dt = min(f_inc dt, dt_max), alpha *= f_alpha;
  *     on P <= 0: Npos = 0, Nneg += 1; unless still inside the initial
- *     delay, dt = max(f_dec dt, dt_min) and alpha = alpha0; then
- *     x -= (dt/2) v and v = 0;
- *   - v += dt F/m; if P > 0, v = (1-alpha) v + alpha |v| F/|F| with norms
- *     over all atoms; x += dt v; F = F(x).
+ *     delay, dt is multiplied by f_dec only when f_dec dt >= dt_min (it is
+ *     left as it is otherwise) and alpha = alpha0; then x -= (dt/2) v and
+ *     v = 0;
+ *   - the MD integration step, the same on both branches: v += dt F/m;
+ *     v = (1-alpha) v + alpha |v| F/|F| with norms over all atoms (after a
+ *     P <= 0 step v = dt F/m, which the mixing leaves alone only when all
+ *     masses are equal); x += dt v; F = F(x).
  * The paper's own stop criteria (Sec. II.B), each off when 0: the average
  * pair energy E_pair/N below e_thres; or the fractional energy drop
  * |(E_{i+1} - E_i)/E_i| (Eq. (6)) below f_thres for ten consecutive
@@ -683,7 +686,7 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
             nneg++;
             if (nneg > p->n_neg_max) { status = 2; break; }
             if (!(p->initial_delay && it < p->n_delay)) {
-                dt = fmax(dt * p->f_dec, p->dt_min);
+                if (dt * p->f_dec >= p->dt_min) dt *= p->f_dec;
                 alpha = p->alpha0;
             }
             for (int64_t i = 0; i < N; ++i) {
@@ -703,7 +706,7 @@ int orc_fire(int d, int64_t N, double L, double *x, double *v, int32_t *img,
             double m = mass ? mass[i] : 1.0;
             for (int k = 0; k < d; ++k) v[i * d + k] += dt * F[i * d + k] / m;
         }
-        if (P > 0.0) {
+        {
             double vv = 0.0, ff = 0.0;
             for (int64_t a = 0; a < N * d; ++a) { vv += v[a] * v[a]; ff += F[a] * F[a]; }
             double vn = sqrt(vv), fn = sqrt(ff);

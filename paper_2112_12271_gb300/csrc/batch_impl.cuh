@@ -200,7 +200,7 @@ __device__ void blk_fire_update(BatchJob &J, const Dev &dv) {
     const double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
     const bool up = fs[FS_BRANCH] != 0.0;
     const double vn = fs[FS_VNORM], fn = fs[FS_FNORM];
-    const bool mix = up && fn > 0.0;
+    const bool mix = fn > 0.0;
     const double cf = mix ? alpha * vn / fn : 0.0;
     for (int k = 0; k < D; ++k) {
         for (int i = threadIdx.x; i < dv.N; i += BT) {

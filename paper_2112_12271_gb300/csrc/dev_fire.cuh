@@ -2,7 +2,10 @@
 // Sci. 175, 109584 (2020); Sec. II.B of the paper names the method), run by one
 // thread after the force reduction of an iteration.  fs holds the state and
 // parameters (FireSlot indices), red the reduced sums (Red indices) of the
-// forces and velocities at the current positions.  Order of tests: converged
+// forces and velocities at the current positions.  The steps are those of the
+// published FIRE 2.0 algorithm (its Algorithm 2): on P <= 0, dt *= f_dec
+// only while f_dec dt >= dt_min, and the velocity mixing belongs to the MD
+// integration step of every iteration.  Order of tests: converged
 // (max_i |F_i| < f_tol; or the paper's criteria of Sec. II.B when set:
 // E_pair/N < e_thres, or the fractional drop below f_thres ten iterations
 // in a row), precision switch, max_iter; then the P = F.v rules.
@@ -46,9 +49,6 @@ __device__ __forceinline__ int fire_scalar_update(double *fs, const double *red)
                 alpha *= fs[FP_FALPHA];
             }
             fs[FS_BRANCH] = 1.0;
-            // |v + dt F/m| expanded over the sums of this reduction
-            fs[FS_VNORM] = sqrt(fmax(red[R_VV] + 2.0 * dt * red[R_VF] + dt * dt * red[R_FF], 0.0));
-            fs[FS_FNORM] = sqrt(red[R_FN]);
         } else {
             fs[FS_NPOS] = 0.0;
             fs[FS_NNEG] += 1.0;
@@ -57,12 +57,20 @@ __device__ __forceinline__ int fire_scalar_update(double *fs, const double *red)
             // been reached, so the FP64 phase takes over; otherwise FIRE fails
             if (fs[FS_NNEG] > fs[FP_NNEGMAX])
                 status = fs[FP_SWITCH] > 0.0 ? FIRE_SWITCH : FIRE_NEGFAIL;
+            // the back-off of dt stops short of dt_min (dt is left as it is
+            // when f_dec dt would fall below it)
             if (!(fs[FP_INITDELAY] != 0.0 && fs[FS_ITER] < fs[FP_NDELAY])) {
-                dt = fmax(dt * fs[FP_FDEC], fs[FP_DTMIN]);
+                if (dt * fs[FP_FDEC] >= fs[FP_DTMIN]) dt *= fs[FP_FDEC];
                 alpha = fs[FP_ALPHA0];
             }
             fs[FS_BRANCH] = 0.0;
         }
+        // |v'| of v' = v + dt F/m (v = 0 after a P <= 0 step), expanded over
+        // the sums of this reduction, for the mixing of every MD step
+        const double vv = P > 0.0 ? red[R_VV] + 2.0 * dt * red[R_VF] + dt * dt * red[R_FF]
+                                  : dt * dt * red[R_FF];
+        fs[FS_VNORM] = sqrt(fmax(vv, 0.0));
+        fs[FS_FNORM] = sqrt(red[R_FN]);
         fs[FS_DT] = dt;
         fs[FS_ALPHA] = alpha;
         if (status == FIRE_RUNNING) {

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
     __shared__ double sh[(NT / 32) * kNRed];
     __shared__ FT sF[NT * D];
     __shared__ FT sE[NT], sW[NT];
-    __shared__ float sD2[NT];
+    __shared__ float sDl[NT * D];   // (float) dlt of the drift, summed per atom in axis order
     __shared__ float sPos[FP64P ? 1 : NT * RF];
     __shared__ int sBad;
     if (cfg.fire_red && dv.flags->fire[FS_STATUS] != (double)FIRE_RUNNING) return;  // loop ended
@@ -181,7 +181,6 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
             sW[al] = w;
         }
     }
-    if (g == 0) sD2[al] = 0.f;
     __syncthreads();
 
     // ---- phase B: (axis, atom) items
@@ -224,7 +223,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
             const double dl = dv.dlt[o] + cfg.dt * v;
             dv.dlt[o] = dl;
             const float fl = (float)dl;
-            atomicAdd(&sD2[a], fl * fl);
+            sDl[a * D + k] = fl;
             if (FP64P) dv.gd[cfg.out_buf][(size_t)ii * RD + k] = dv.x0[o] + dl;
             else sPos[a * RF + k] = dv.gs0[(size_t)ii * RF + k] + fl;
         }
@@ -259,15 +258,21 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
             for (int a = threadIdx.x; a < APB; a += NT)
                 if (base + a < dv.N) dv.gd[cfg.out_buf][(size_t)(base + a) * RD + D] = 0.5 * dv.sigma[base + a];
         }
-        float m = 0.f;
+        unsigned mb = 0u;   // max of the float bits: a NaN orders above every number
         int half = 0;
         const float q2 = (float)(0.25 * dv.skin * dv.skin);
         for (int a = threadIdx.x; a < APB; a += NT) {
-            m = fmaxf(m, sD2[a]);
-            half += base + a < dv.N && sD2[a] >= q2;
+            if (base + a >= dv.N) continue;
+            // |dlt|^2 of one atom, summed by one thread in axis order, so the
+            // trigger (and the rebuild step it picks) repeats bit for bit
+            float d2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) d2 = fmaf(sDl[a * D + k], sDl[a * D + k], d2);
+            mb = max(mb, __float_as_uint(d2));
+            half += d2 >= q2;
         }
         const int blk_half = cfg.rule == 1 ? __syncthreads_count(half) : 0;   // APB <= NT
-        trigger_fold(dv, m, false, cfg.cond_rebuild, nvt ? 1 : 0, kin, cfg.nvt_rate, cfg.nvt_T,
+        trigger_fold(dv, __uint_as_float(mb), false, cfg.cond_rebuild, nvt ? 1 : 0, kin, cfg.nvt_rate, cfg.nvt_T,
                      cfg.rule, cfg.n_bet, blk_half);
     }
     if (cfg.thermo || cfg.fire_red) {
@@ -284,7 +289,8 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
 
 // FIRE per-atom update, from the scalars the last force reduction left:
 //   P <= 0 branch: x -= dt v / 2, v = 0;
-//   v += dt F/m;  P > 0 branch: v = (1-alpha) v + alpha |v| F/|F|;  x += dt v.
+//   then on both branches v += dt F/m; v = (1-alpha) v + alpha |v| F/|F|;
+//   x += dt v.
 // Block = NT/4 atoms; (axis, atom) items over all threads as in k_step.
 template <int D>
 __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
@@ -292,20 +298,18 @@ __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
     constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
     constexpr int APB = NT / 4;
     __shared__ float sPos[APB * RF];
-    __shared__ float sD2[APB];
+    __shared__ float sDl[APB * D];
     __shared__ double sBack[APB * D], sStep[APB * D], sCB[APB], sCS[APB];
     const double *fs = dv.flags->fire;
     if (fs[FS_STATUS] != (double)FIRE_RUNNING) return;
     const double dt = fs[FS_DT], alpha = fs[FS_ALPHA];
     const bool up = fs[FS_BRANCH] != 0.0;
     const double vn = fs[FS_VNORM], fn = fs[FS_FNORM];
-    const bool mix = up && fn > 0.0;
+    const bool mix = fn > 0.0;
     const double cf = mix ? alpha * vn / fn : 0.0;
     const double dxm = fs[FP_DXMAX];
     const int base = blockIdx.x * APB;
     const int Np = dv.Npad;
-    for (int a = threadIdx.x; a < APB; a += NT) sD2[a] = 0.f;
-    __syncthreads();
     if (dxm > 0.0) {
         // Table II's displacement cap: an atom whose back-off (dt/2) v or
         // step dt v is longer than dx_max moves dx_max along it; the
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
         }
         dv.dlt[o] = dl;
         const float fl = (float)dl;
-        atomicAdd(&sD2[a], fl * fl);
+        sDl[a * D + k] = fl;
         sPos[a * RF + k] = dv.gs0[(size_t)ii * RF + k] + fl;
         if (write_fp64_rows) dv.gd[0][(size_t)ii * RD + k] = dv.x0[o] + dl;
     }
@@ -373,9 +377,15 @@ __global__ void __launch_bounds__(NT) k_fire_update(Dev dv, int write_fp64_rows,
     if (write_fp64_rows)
         for (int a = threadIdx.x; a < APB; a += NT)
             if (base + a < dv.N) dv.gd[0][(size_t)(base + a) * RD + D] = 0.5 * dv.sigma[base + a];
-    float m = 0.f;
-    for (int a = threadIdx.x; a < APB; a += NT) m = fmaxf(m, sD2[a]);
-    trigger_fold(dv, m, false, cond_rebuild);
+    unsigned mb = 0u;   // max of the float bits: a NaN orders above every number
+    for (int a = threadIdx.x; a < APB; a += NT) {
+        if (base + a >= dv.N) continue;
+        float d2 = 0.f;   // one thread per atom, axis order: repeatable
+#pragma unroll
+        for (int k = 0; k < D; ++k) d2 = fmaf(sDl[a * D + k], sDl[a * D + k], d2);
+        mb = max(mb, __float_as_uint(d2));
+    }
+    trigger_fold(dv, __uint_as_float(mb), false, cond_rebuild);
 }
 
 // write gather rows of buffer buf from x0 + dlt (FP32 and/or FP64 rows)

@@ -139,6 +139,27 @@ def test_md_in_pieces_equals_one_call_and_is_deterministic(H):
     assert np.abs(outs[0]["x"] - outs[1]["x"]).max() < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_rebuild_schedule_repeats_bitwise(H, prec):
+    """The trigger's |dlt|^2 is summed per atom in axis order (no atomics),
+    so the same start gives the same rebuild steps and the same bits: three
+    runs of 600 steps of a hot d = 6 system that rebuilds every few steps
+    (many trigger evaluations close to the threshold s/2)."""
+    s = W.make_system(6, 4000, L=5.6, dist="poly", T=0.5, seed=17)
+    p = H.HDMD_MIXED if prec == "mixed" else H.HDMD_FP64
+    outs = []
+    for _ in range(3):
+        with H.System(s.d, s.L, s.sigma, s.x, s.v, precision=p) as g:
+            t = g.md_steps(600, 0.005)
+            outs.append((g.state(), t))
+    assert outs[0][1]["rebuilds"] >= 30
+    for st, t in outs[1:]:
+        assert t["rebuilds"] == outs[0][1]["rebuilds"]
+        assert np.array_equal(st["x"], outs[0][0]["x"])
+        assert np.array_equal(st["v"], outs[0][0]["v"])
+        assert t["E_pair"] == outs[0][1]["E_pair"]
+
+
 def test_graphs_and_eager_paths_agree(H):
     s = W.make_system(6, 3000, L=5.2, dist="poly", T=1e-3, seed=11)
     res = []
@@ -260,6 +281,42 @@ def test_fire_first_iterations_follow_oracle(H):
         dx -= s.L * np.round(dx / s.L)
         assert np.abs(dx).max() < 1e-10, (it, np.abs(dx).max())
         assert r["E_pair"] == pytest.approx(ref["E"], rel=1e-10)
+
+
+def test_fire_dt_floor_and_mixing_with_masses_follow_oracle(H):
+    """FIRE 2.0 as published, where the two readings of its back-off and
+    mixing part: masses sigma^3 of unequal size (so the mixing after a
+    restart from rest moves v off F/m), and dt_max = 0.0095 below
+    dt_min / f_dec = 0.0098, so the P < 0 step at iteration 128 keeps dt
+    (a floor at dt_min would set it to 0.0049).  Positions after 1, 127,
+    128, 129 and 160 iterations, and the iteration count at convergence,
+    against the oracle; the mixed precision path at the end too."""
+    x = np.array([[0.0, 0.0, 0.0], [0.3, 0.05, 0.0], [1.8, 0.0, 0.0],
+                  [-4.0, 0.0, 0.0], [-4.0, 0.9, 0.0]])
+    sig = np.array([1.0, 1.0, 1.4, 1.2, 0.9])
+    m, L = sig ** 3, 12.0
+    kw = dict(dt_min=0.0049, dt_max=0.0095)
+    a = oracle.fire(x, sig, L, mass=m, max_iter=128, **kw)
+    assert float((a["F"] * a["v"]).sum()) < 0     # the P < 0 step the test is about
+    for it in (1, 127, 128, 129, 160, None):
+        p = dict(kw) if it is None else dict(kw, max_iter=it)
+        ref = oracle.fire(x, sig, L, mass=m, **p)
+        for prec in ((H.HDMD_FP64, H.HDMD_MIXED) if it is None else (H.HDMD_FP64,)):
+            with H.System(3, L, sig, x, None, m, precision=prec) as g:
+                r = g.fire(**p)
+                xs = g.state()["x"]
+            if it is not None:
+                assert r["iterations"] == ref["iters"] == it
+            else:
+                assert ref["status"] == 0 and r["converged"]
+                if prec == H.HDMD_FP64:
+                    assert r["iterations"] == ref["iters"]
+            dx = xs - ref["x"]
+            dx -= L * np.round(dx / L)
+            # mixed: FP32 pair forces until the FP64 polish, so the path to
+            # the (flat, E = 0) minimum differs by their rounding
+            tol = 1e-10 if prec == H.HDMD_FP64 else 1e-4
+            assert np.abs(dx).max() < tol, (it, prec, np.abs(dx).max())
 
 
 # ------------------------------------------------------------------ SWAP

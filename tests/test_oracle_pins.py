@@ -808,20 +808,87 @@ def _collision_scene():
     return x, np.ones(5), 12.0
 
 
-def test_fire_dt_floor_at_the_negative_power_step(orc):
-    """On P <= 0 past the initial delay dt = max(f_dec dt, dt_min): with
-    dt_min above f_dec dt_max the step after the collision uses dt_min (the
-    velocity restarts from rest, v = dt F)."""
+def _dt_of_step(a, b, L):
+    """dt of the iteration from state a to state b, read off x_b - x_a =
+    dt v_b (no displacement cap)."""
+    dx = b["x"] - a["x"]
+    dx -= L * np.round(dx / L)
+    return float((dx * b["v"]).sum() / (b["v"] * b["v"]).sum())
+
+
+@pytest.mark.parametrize("dt_min,halves", [(0.015, False), (1e-4, True)])
+def test_fire_dt_back_off_only_above_dt_min(orc, dt_min, halves):
+    """FIRE 2.0 (Guenole et al. 2020, Algorithm 2): on P <= 0 past the
+    initial delay dt is multiplied by f_dec only when f_dec dt >= dt_min, and
+    is left unchanged otherwise.  With dt_min = 0.015 above f_dec dt at the
+    collision (dt <= dt_max = 0.02) the step after it runs with the dt of the
+    step before (a floor at dt_min would give 0.015 instead, raising a dt
+    below dt_min to it); with the default dt_min it runs with f_dec dt.  The
+    velocity restarts from rest (v = dt F, unit masses)."""
     x, sig, L = _collision_scene()
-    kw = dict(dt_max=0.02, dt_min=0.015)
-    prev = None
-    for k in range(1, 200):
-        a = orc.fire(x, sig, L, max_iter=k, **kw)
-        if k > 20 and float((a["F"] * a["v"]).sum()) <= 0:
-            b = orc.fire(x, sig, L, max_iter=k + 1, **kw)
+    kw = dict(dt_max=0.02, dt_min=dt_min)
+    runs = {}
+
+    def run(k):
+        if k not in runs:
+            runs[k] = orc.fire(x, sig, L, max_iter=k, **kw)
+        return runs[k]
+
+    for k in range(22, 200):
+        a = run(k)
+        if float((a["F"] * a["v"]).sum()) <= 0:
+            b = run(k + 1)
             dt = np.linalg.norm(b["v"]) / np.linalg.norm(a["F"])
-            assert dt == pytest.approx(0.015, rel=1e-9)
             assert np.abs(b["v"] - dt * a["F"]).max() <= 1e-12 * np.abs(b["v"]).max()
+            dt_before = _dt_of_step(run(k - 1), a, L)
+            assert 0.005 <= dt_before <= 0.02 * (1 + 1e-9)
+            if halves:
+                assert dt == pytest.approx(0.5 * dt_before, rel=1e-9)
+            else:
+                assert 0.5 * dt_before < dt_min
+                assert dt == pytest.approx(dt_before, rel=1e-9)
+            return
+    pytest.fail("no P <= 0 step")
+
+
+def test_fire_mixing_in_every_step_with_masses(orc):
+    """FIRE 2.0 mixes v = (1 - alpha) v + alpha |v| F/|F| in every MD
+    integration step, after v += dt F/m.  With unequal masses m = sigma^d
+    the first iteration (P = 0 from rest, a P <= 0 step inside the initial
+    delay: dt = dt0, alpha = alpha0) therefore gives, in closed form,
+    v_1 = (1 - alpha0) dt0 F/m + alpha0 dt0 |F/m| F/|F| (norms over all atoms)
+    and x_1 = x_0 + dt0 v_1; mixing only on P > 0 would give v_1 = dt0 F/m.
+    The same form holds at a later P <= 0 step past the delay, with
+    alpha = alpha0 and dt = f_dec dt_before."""
+    x, _, L = _collision_scene()
+    x[2, 0] = 1.8
+    sig = np.array([1.0, 1.0, 1.4, 1.2, 0.9])   # the pushed sphere meets a heavy one
+    m = sig ** 3
+    dt0, alpha0 = 0.005, 0.25
+    F0, _, _ = orc.forces(x, sig, L)
+    a1 = dt0 * F0 / m[:, None]
+    v1 = (1 - alpha0) * a1 + alpha0 * np.linalg.norm(a1) * F0 / np.linalg.norm(F0)
+    r1 = orc.fire(x, sig, L, mass=m, max_iter=1)
+    assert np.abs(r1["v"] - v1).max() <= 1e-13 * np.abs(v1).max()
+    dx = r1["x"] - x
+    dx -= L * np.round(dx / L)
+    # positions carry the rounding of coordinates up to |x| = 4
+    assert np.abs(dx - dt0 * v1).max() <= 4 * np.finfo(float).eps * np.abs(x).max()
+    # the mixing changes v_1 by much more than rounding
+    assert np.abs(v1 - a1).max() > 1e-3 * np.abs(a1).max()
+    kw = dict(dt_max=0.02)
+    for k in range(22, 200):
+        a = orc.fire(x, sig, L, mass=m, max_iter=k, **kw)
+        if float((a["F"] * a["v"]).sum()) < 0:
+            b = orc.fire(x, sig, L, mass=m, max_iter=k + 1, **kw)
+            prev = orc.fire(x, sig, L, mass=m, max_iter=k - 1, **kw)
+            dxp = a["x"] - prev["x"]
+            dxp -= L * np.round(dxp / L)
+            dt_before = float((dxp * a["v"]).sum() / (a["v"] * a["v"]).sum())
+            dt = 0.5 * dt_before
+            ak = dt * a["F"] / m[:, None]
+            vk = (1 - alpha0) * ak + alpha0 * np.linalg.norm(ak) * a["F"] / np.linalg.norm(a["F"])
+            assert np.abs(b["v"] - vk).max() <= 1e-9 * np.abs(vk).max()
             return
     pytest.fail("no P <= 0 step")
 
