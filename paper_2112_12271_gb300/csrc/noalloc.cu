@@ -1,18 +1,20 @@
 // noalloc.cu -- forces, energy and virial without any device allocation.
 //
 // Some callers cannot allocate GPU memory at the point where they need
-// forces: code running while a CUDA graph is being captured (cudaMalloc is
-// not capturable), plug-ins that live inside a host framework whose memory
-// pool owns the device, or real-time loops that forbid allocation after
-// start-up.  compute_forces_noalloc serves them: the caller passes device
+// forces: plug-ins that live inside a host framework whose memory pool owns
+// the device, or loops that forbid allocation after start-up (an allocation
+// may wait on the whole device).  compute_forces_noalloc serves them: the
+// caller passes device
 // buffers for the inputs and outputs, and the only other memory the kernel
 // touches is the file-scope scratch array below, which the library holds on
 // every GPU it is loaded on until the process exits.
 //
 // The kernel is the FP64 form of the force / energy / virial evaluation with
-// the list replaced by all pairs, so it needs no Verlet list and no cell
-// arrays; its scratch is the per-block partial sums of the deterministic
-// energy/virial reduction plus the last-block ticket.
+// the list replaced by all pairs (O(N^2 d) FP64 work), so it needs no Verlet
+// list and no cell arrays; its scratch is the per-block partial sums of the
+// deterministic energy/virial reduction plus the last-block ticket.  Each
+// pair is taken at its nearest image, the only one that can overlap while
+// L >= 2 max sigma (the caller's precondition).
 #include <cuda_runtime.h>
 #include <stdint.h>
 

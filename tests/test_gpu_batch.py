@@ -85,6 +85,29 @@ def test_batch_md_matches_oracle_and_system(H):
     assert r["K"] == pytest.approx(ref["K"], rel=1e-10)
 
 
+@pytest.mark.parametrize("d,N,kw", [(3, 1000, dict(phi=0.6)), (6, 3000, dict(L=5.0))])
+def test_batch_mixed_md_matches_oracle(H, d, N, kw):
+    """The mixed-precision batched MD that the serving loop runs (FP32 pair
+    forces, FP64 kick and drift): 100 steps against the FP64 oracle within
+    the mixed trajectory tolerance of the single-system tests (1e-5 of the
+    positions, E and K relative), beside a different job in the same batch."""
+    s = W.make_system(d, N, dist="poly", T=1e-3, seed=40 + d, **kw)
+    other = W.make_system(4, 500, phi=0.3, dist="bi", T=1e-3, seed=9)
+    ref = oracle.md_steps(s.x, s.v, s.sigma, s.L, 100, 0.005)
+    assert ref["builds"] >= 1
+    with H.Batch(pool_bytes=128 << 20, max_jobs=4, precision=H.HDMD_MIXED) as b:
+        jid = b.add(H.JOB_MD, d, s.L, s.sigma, s.x, s.v, dt=0.005, nsteps=100)
+        b.add(H.JOB_MD, 4, other.L, other.sigma, other.x, other.v, dt=0.005, nsteps=60)
+        b.run(0)
+        r = b.result(jid, positions=True)
+    assert r["status"] == H.JOB_DONE and r["iterations"] == 100
+    dx = r["x"] - ref["x"]
+    dx -= s.L * np.round(dx / s.L)
+    assert np.abs(dx).max() < 1e-5
+    assert r["E_pair"] == pytest.approx(ref["E"], rel=1e-5)
+    assert r["K"] == pytest.approx(ref["K"], rel=1e-5)
+
+
 def test_batch_admission_by_pool_memory(H):
     s = W.make_system(4, 2000, phi=0.3, dist="bi", T=0.0, seed=3)
     with H.Batch(pool_bytes=8 << 20, max_jobs=32, precision=H.HDMD_MIXED) as b:
