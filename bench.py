@@ -143,12 +143,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- CPU arms
-def oracle_md_sample(sysd, nsteps):
-    """Time the FP64 oracle on nsteps of the workload (list build included)."""
+def oracle_md_sample(sysd, nsteps, openmp=False):
+    """Time the FP64 oracle on nsteps of the workload (the list build at the
+    start of the call included); openmp=True runs its threaded build."""
     import oracle
-    oracle.build()
+    oracle.build(openmp=openmp)
     t0 = time.perf_counter()
-    out = oracle.md_steps(sysd.x, sysd.v, sysd.sigma, sysd.L, nsteps, DT)
+    out = oracle.md_steps(sysd.x, sysd.v, sysd.sigma, sysd.L, nsteps, DT, openmp=openmp)
     dt = time.perf_counter() - t0
     return dt, out
 
@@ -168,44 +169,225 @@ def host_cpu():
     return {"cpu": model, "nproc": os.cpu_count()}
 
 
-def cpu_baseline(sysd, nsteps=100):
-    dt, _ = oracle_md_sample(sysd, nsteps)
-    return {"value": sysd.N * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+def oracle_threads():
+    """Set the OpenMP oracle to every host core; returns the count it uses."""
+    import oracle
+    oracle.build(openmp=True)
+    return oracle.set_threads(os.cpu_count() or 1)
+
+
+def cpu_baselines(sysd, n_serial=100, n_omp=200):
+    """The oracle timed on the host: serially on one core (n_serial steps),
+    and its OpenMP build on every core (n_omp steps, per-atom force and
+    integration loops and the per-subcell list build run in parallel, as in
+    the paper's scheme).  Each call builds the list once at its start, then
+    whenever the trigger fires."""
+    dt1, o1 = oracle_md_sample(sysd, n_serial)
+    serial = {"value": sysd.N * n_serial / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+              **host_cpu(),
+              "sample": "%d VV timesteps of the same d=6 N=32768 system (%d list builds), "
+                        "serial FP64 C, %.1f s" % (n_serial, o1["builds"], dt1)}
+    nt = oracle_threads()
+    dtn, on = oracle_md_sample(sysd, n_omp, openmp=True)
+    allc = {"value": sysd.N * n_omp / dtn, "unit": UNIT, "cores": nt, "kind": "oracle",
             **host_cpu(),
-            "sample": "%d VV timesteps of the same d=6 N=32768 system (one cell-list "
-                      "build + %d force evaluations), serial FP64 C, %.1f s" % (nsteps, nsteps, dt)}
+            "sample": "%d VV timesteps of the same d=6 N=32768 system (%d list builds), "
+                      "FP64 C, OpenMP on %d threads, %.1f s" % (n_omp, on["builds"], nt, dtn)}
+    return allc, serial
+
+
+REF_PER_STEP = 200   # oracle timesteps per bench step of the reference arm
 
 
 def run_reference(args):
+    """The oracle on every host core, on the workload of the GPU arm: each
+    bench step continues the trajectory for REF_PER_STEP timesteps (lists
+    rebuilt when the trigger fires, plus once at the start of each call)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle
     s = W.c1_poly_d6()
-    per = 20    # oracle timesteps per bench step (a bounded sample)
+    nt = oracle_threads()
+    x, v, img = s.x, s.v, None
     for _ in range(args.warmup):
-        oracle_md_sample(s, 5)
-    t = 0.0
+        oracle_md_sample(s, 5, openmp=True)
+    t, builds = 0.0, 0
     for _ in range(args.steps):
-        dt, _ = oracle_md_sample(s, per)
-        t += dt
-    value = s.N * per * args.steps / t
+        t0 = time.perf_counter()
+        out = oracle.md_steps(x, v, s.sigma, s.L, REF_PER_STEP, DT, img=img, openmp=True)
+        t += time.perf_counter() - t0
+        x, v, img = out["x"], out["v"], out["img"]
+        builds += out["builds"]
+    value = s.N * REF_PER_STEP * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": s.N, "d": 6,
-                       "timesteps_per_step": per, "l2": "cpu"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD, "N": s.N, "d": 6, "dt": DT, "skin": 0.3,
+                       "timesteps_per_step": REF_PER_STEP, "l2": "cpu",
+                       "list_builds": builds},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
                              **host_cpu(),
-                             "sample": "%d VV timesteps per step, serial FP64 C oracle "
-                                       "(list build each step)" % per},
+                             "sample": "%d VV timesteps per bench step continuing one "
+                                       "trajectory, FP64 C oracle with OpenMP on %d threads "
+                                       "(%d list builds in all)" % (REF_PER_STEP, nt, builds)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+# --------------------------------------------------------------------- roofline
+def alg_bytes_per_atom_step(d, Z, b_F):
+    """Algorithmic bytes of one atom-step of the fused force + velocity-Verlet
+    kernel: the list once (4 Z), its length (4), the diameter (4), x read
+    and written (16 d), v read and written (16 d), F written and read
+    (2 b_F d, b_F = 4 in mixed precision, 8 in FP64); neighbour coordinates
+    are taken as cache-resident (atoms are in subcell order)."""
+    return 4.0 * Z + 4 + 4 + 16 * d + 16 * d + 2 * b_F * d
+
+
+def design_bytes_per_atom_step(d, Z):
+    """What the mixed kernel of this design moves per atom-step: 8-byte list
+    entries (index + subcell-offset code), the length, v and dlt read and
+    written in FP64, and three FP32 rows (own, build-time, new)."""
+    RF = (d + 1 + 3) & ~3
+    return 8.0 * Z + 4 + 16 * d + 16 * d + 3 * 4 * RF
+
+
+# DRAM bytes per launch of the fused step kernel, dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the current kernel on each
+# workload (the commands are in profiles/); None where the kernel has changed
+# since its last capture
+TRAFFIC = {"c1": None, "c1l": None}
+
+
+def roofline_record(s, info, step_ms, workload, b_F=4):
+    d = s.d
+    Z = info["total_list_entries"] / s.N
+    bpa = alg_bytes_per_atom_step(d, Z, b_F)
+    achieved = bpa * s.N / (step_ms * 1e-3) / 1e9 if step_ms else None
+    peak, peak_kind = peaks()
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": TRAFFIC.get(workload),
+            "kernel": "k_step<%d,%s> (pair forces + kicks + drift + trigger)"
+                      % (d, "mixed" if b_F == 4 else "fp64"),
+            "bytes_per_atom_step": bpa, "N": s.N, "mean_list_length": Z,
+            "design_bytes_per_atom_step": design_bytes_per_atom_step(d, Z),
+            "peak_kind": peak_kind, "l2_bytes": l2_bytes(),
+            "footprint_bytes": footprint_bytes(s)}
+
+
 # --------------------------------------------------------------------- GPU arm
+def c1l_record(hdmd, stream, flush, steps=100):
+    """The same density with N = 2^21 (L = 12): the system (3.5 GB) does not
+    fit in L2, so the step kernel streams from HBM.  Average duration of the
+    fused step kernel (CUDA events, 20 launches) and the MD rate of one
+    100-step run after an L2 flush."""
+    import torch
+    s = W.c1_poly_d6(N=2 ** 21)
+    with hdmd.System(s.d, s.L, s.sigma, s.x, s.v, precision=hdmd.HDMD_MIXED,
+                     stream=stream.cuda_stream) as g:
+        g.md_steps(20, DT)
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t = g.md_steps(steps, DT)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        info = g.info()
+        prof = g.profile(reps=20, dt=DT)
+    return {"workload": "d6_N2097152_polydisperse_harmonic_L12_NVE_dt0.005_skin0.3",
+            "value": s.N * steps / (ms / 1000.0), "unit": UNIT, "timesteps": steps,
+            "rebuilds": t["rebuilds"], "kernel_ms": prof,
+            "roofline": roofline_record(s, info, prof["step_ms"], "c1l")}
+
+
+def batch_pool_bytes(specs):
+    return sum(2500 * sp["N"] * sp["d"] for sp in specs) + (256 << 20)
+
+
+def batch_pass(hdmd, stream, systems, precision, max_iter, autotune=True):
+    """One launch of the batched engine over every job (to the end); returns
+    (device ms, results, lanes by d)."""
+    import torch
+    specs = [dict(N=s.N, d=s.d) for s in systems]
+    b = hdmd.Batch(pool_bytes=batch_pool_bytes(specs), max_jobs=len(systems) + 8,
+                   precision=precision, stream=stream.cuda_stream)
+    try:
+        ids = [b.add(hdmd.JOB_FIRE, s.d, s.L, s.sigma, s.x, max_iter=max_iter) for s in systems]
+        assert all(i is not None for i in ids)
+        if autotune:
+            b.autotune(reps=2)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        c = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.run(0)
+        c.record(stream)
+        c.synchronize()
+        res = [b.result(i) for i in ids]
+        lanes = b.info()["lanes"]
+    finally:
+        b.close()
+    return a.elapsed_time(c), res, lanes
+
+
+def c3_record(hdmd, stream, jobs=512, max_iter=20000):
+    """512 FIRE minimisations (d 3-6, N 256-8192) to max|F_i| < 1e-10 in one
+    persistent launch: mixed precision with the FP64 polish against the plain
+    FP64 form of the same engine on the same jobs."""
+    specs = W.c3_batch_specs(jobs, seed=0)
+    systems = [W.c3_job(sp) for sp in specs]
+    batch_pass(hdmd, stream, systems[:32], hdmd.HDMD_MIXED, max_iter)   # warm-up
+    out = {"workload": "batch_fire_%d_d3-6_N256-8192_bidisperse" % jobs, "jobs": jobs,
+           "atoms": sum(s.N for s in systems), "max_iter": max_iter, "unit": "jobs/s"}
+    for name, prec in (("mixed", hdmd.HDMD_MIXED), ("fp64", hdmd.HDMD_FP64)):
+        ms, res, lanes = batch_pass(hdmd, stream, systems, prec, max_iter)
+        conv = sum(1 for r in res if r["converged"])
+        out[name] = {"value": conv / (ms / 1000.0), "converged": conv, "seconds": ms / 1000.0,
+                     "max_fmax_converged": max((r["fmax"] for r in res if r["converged"]),
+                                               default=None),
+                     "fire_iterations": sum(r["iterations"] for r in res),
+                     "lanes_by_d": lanes[3:7]}
+    out["value"] = out["mixed"]["value"]
+    out["speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def c4_record(serve_seconds=2.0, slots=16, small_n=1024, budget=256, pool_gb=2, policy="sjf",
+              seq_sample=24, time_limit=300.0):
+    """A fixed slice of the serving stream (the first serve_seconds of the
+    Poisson arrivals at 200 requests/s): jobs/s and p50/p99 latency through
+    the continuous-batching server, beside the first seq_sample requests
+    served one after another as plain FP64 systems and by the server."""
+    from paper_2112_12271_gb300 import serve
+    from paper_2112_12271_gb300 import hdmd
+    reqs = W.c4_requests(duration=serve_seconds, rate=200.0, seed=0)
+    systems = [W.c4_system(r) for r in reqs]
+    warm = W.c4_requests(duration=0.05, rate=200.0, seed=1)
+    kw = dict(precision=hdmd.HDMD_MIXED, slots=slots, small_N=small_n,
+              batch_pool_bytes=pool_gb << 30, budget=budget, policy=policy)
+    srv = serve.Server(**kw)
+    srv.run(warm, [W.c4_system(r) for r in warm])
+    summ = serve.summarize(srv.run(reqs, systems, time_limit=time_limit))
+    srv.close()
+    k = min(seq_sample, len(reqs))
+    seq = serve.summarize(serve.sequential_fp64(reqs[:k], systems[:k]))
+    srv2 = serve.Server(**kw)
+    sub = serve.summarize(srv2.run(reqs[:k], systems[:k]))
+    srv2.close()
+    return {"workload": "serve_poisson200_md_fire_d3-8_N256-131072",
+            "slice": "first %.1f s of arrivals (%d requests)" % (serve_seconds, len(reqs)),
+            "value": summ["jobs_per_s"], "unit": "jobs/s", "latency_p50_s": summ["p50_s"],
+            "latency_p99_s": summ["p99_s"], "summary": summ, "policy": policy,
+            "first_%d_requests" % k: {"server": sub, "sequential_fp64": seq}}
+
+
 def run_gpu(args):
     import torch
     from paper_2112_12271_gb300 import build as B
@@ -266,32 +448,39 @@ def run_gpu(args):
     info = g.info()
     prof = g.profile(reps=50, dt=DT) if not args.no_profile else None
 
-    # end to end: host state in (pinned), md_steps, thermo out, per step
+    # end to end through the public API: host state in (pinned), md_steps,
+    # positions and velocities back out (pinned), per step
+    nd = s.N * s.d
     xh = torch.from_numpy(np.ascontiguousarray(s.x)).pin_memory().numpy()
     vh = torch.from_numpy(np.ascontiguousarray(s.v)).pin_memory().numpy()
+    xo = torch.empty((s.N, s.d), dtype=torch.float64).pin_memory().numpy()
+    vo = torch.empty((s.N, s.d), dtype=torch.float64).pin_memory().numpy()
     e2e_ms = []
     for k in range(0 if args.no_e2e else args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.set_state(xh, vh)
         g.md_steps(md_per_step, DT)
-        torch.cuda.synchronize()
+        g.state_into(xo, vo)
         if k >= args.warmup:
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_value = (ws * s.N * md_per_step * args.steps / (sum(e2e_ms) / 1000.0)) if e2e_ms else None
     g.close()
 
-    # FP64 plain form of the same workload (fewer steps: FP64 is slow on GB300)
+    # FP64 plain form of the same workload
     fp64 = None
     if not args.no_fp64:
         g64 = hdmd.System(s.d, s.L, s.sigma, s.x, s.v, precision=hdmd.HDMD_FP64,
                           stream=stream.cuda_stream)
-        k64 = max(1, min(args.steps, 3))
+        k64 = max(1, min(args.steps, 10))
         ms64, _, _ = timed_md(g64, k64, 1)
+        info64 = g64.info()
         prof64 = g64.profile(reps=20, dt=DT) if not args.no_profile else None
         g64.close()
         fp64 = {"value": s.N * md_per_step * k64 / (sum(ms64) / 1000.0), "unit": UNIT,
-                "ms_per_step": sum(ms64) / k64, "steps": k64, "kernel_ms": prof64}
+                "ms_per_step": sum(ms64) / k64, "steps": k64, "kernel_ms": prof64,
+                "roofline": roofline_record(s, info64, prof64["step_ms"] if prof64 else None,
+                                            "none", b_F=8)}
 
     if rank != 0:
         if ws > 1:
@@ -299,18 +488,8 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    # DRAM bytes per launch of the fused step kernel from one ncu capture of
-    # this kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum,
-    # cold L2 as ncu replays it); None where no capture of the current kernel
-    # exists for the workload
-    TRAFFIC = {"c1": 13155072 + 0}
-    # roofline of the dominant kernel: fused force + kicks + drift (mixed)
     d = s.d
-    RF = (d + 1 + 3) & ~3
     Z = info["total_list_entries"] / s.N
-    bytes_per_atom = 8 * Z + 4 + 16 * d + 16 * d + 3 * 4 * RF
-    achieved = bytes_per_atom * s.N / (prof["step_ms"] * 1e-3) / 1e9 if prof else None
-    peak, peak_kind = peaks()
     n_launch = args.steps * (md_per_step + 1) + 6 * rebuilds
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -328,20 +507,23 @@ def run_gpu(args):
                    "rebuilds_per_step": rebuilds / args.steps},
         "fp64": fp64,
         "kernel_ms": prof,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None,
-                     "traffic": TRAFFIC.get(args.workload),
-                     "kernel": "k_step<6,mixed> (pair forces + kicks + drift)",
-                     "bytes_per_atom": bytes_per_atom, "peak_kind": peak_kind,
-                     "l2_bytes": l2_bytes(), "footprint_bytes": footprint_bytes(s)},
+        "roofline": roofline_record(s, info, prof["step_ms"] if prof else None, args.workload),
         "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": 2 * s.N * d * 8,
-                "d2h_bytes_per_step": 7 * 8},
+                "h2d_bytes_per_step": 2 * nd * 8,
+                "d2h_bytes_per_step": 2 * nd * 8 + 7 * 8},
         "gpu_launches": n_launch,
         "clocks": clocks,
     }
+    if ws == 1 and args.workload == "c1" and not args.no_sub:
+        # the other figures the benchmark metric names, each measured here
+        line["c1l"] = c1l_record(hdmd, stream, flush)
+        del flush
+        line["c3_batched_fire"] = c3_record(hdmd, stream, max_iter=args.max_iter)
+        line["c4_serving"] = c4_record(policy=args.policy, slots=args.slots,
+                                       small_n=args.small_n, budget=args.budget,
+                                       pool_gb=args.pool_gb)
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(s)
+        line["cpu_baseline"], line["cpu_baseline_serial"] = cpu_baselines(s)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -352,75 +534,24 @@ def run_gpu(args):
 # --------------------------------------------------------------------- batched FIRE
 def run_batch(args):
     """512 independent FIRE minimisations (to max|F_i| < 1e-10) in the batched
-    engine, mixed precision with FP64 polish; compared with the plain FP64
-    single-system path run one job after another on a bounded sample."""
+    engine, mixed precision with FP64 polish, against the plain FP64 form of
+    the same engine on the same 512 jobs (one pass each)."""
     import torch
     from paper_2112_12271_gb300 import build as B
     from paper_2112_12271_gb300 import hdmd
     torch.cuda.set_device(0)
     B.build()
-    specs = W.c3_batch_specs(args.jobs, seed=0)
-    systems = [W.c3_job(sp) for sp in specs]
     stream = torch.cuda.current_stream()
-    atoms = sum(sp["N"] for sp in specs)
-    pool = sum(2500 * sp["N"] * sp["d"] for sp in specs) + (256 << 20)
-
-    def one_pass():
-        b = hdmd.Batch(pool_bytes=pool, max_jobs=len(specs) + 8, precision=hdmd.HDMD_MIXED,
-                       stream=stream.cuda_stream)
-        ids = [b.add(hdmd.JOB_FIRE, s.d, s.L, s.sigma, s.x, max_iter=args.max_iter)
-               for s in systems]
-        assert all(i is not None for i in ids)
-        if args.autotune:
-            b.autotune(reps=2)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        c = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        left = b.run(0)
-        c.record(stream)
-        c.synchronize()
-        res = [b.result(i) for i in ids]
-        lanes = b.info()["lanes"]
-        b.close()
-        return a.elapsed_time(c), left, res, lanes
-
-    for _ in range(max(1, args.warmup - 2)):
-        one_pass()
-    times, res, lanes = [], None, None
-    for _ in range(args.steps):
-        ms, left, res, lanes = one_pass()
-        times.append(ms)
-    conv = sum(1 for r in res if r["converged"])
-    fmax = max(r["fmax"] for r in res if r["converged"]) if conv else None
-    iters = sum(r["iterations"] for r in res)
-    value = conv * args.steps / (sum(times) / 1000.0)   # converged jobs only
-    # plain FP64 single-system path, one job after another, bounded sample
-    sample = systems[:args.fp64_sample]
-    t0 = time.perf_counter()
-    fp64_conv = 0
-    for s in sample:
-        with hdmd.System(s.d, s.L, s.sigma, s.x, precision=hdmd.HDMD_FP64,
-                         stream=stream.cuda_stream) as g:
-            r = g.fire(max_iter=args.max_iter)
-            fp64_conv += int(r["converged"])
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t0
-    fp64_value = fp64_conv / t64
-    line = {"metric": "batched FIRE jobs/s converged to |F|max<1e-10 (512 jobs, d 3-6, N 256-8192)",
-            "value": value, "unit": "jobs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(times) / args.steps,
+    rec = c3_record(hdmd, stream, jobs=args.jobs, max_iter=args.max_iter)
+    line = {"metric": "batched FIRE jobs/s converged to |F|max<1e-10 (%d jobs, d 3-6, N 256-8192)"
+                      % args.jobs,
+            "value": rec["value"], "unit": "jobs/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1000.0 * rec["mixed"]["seconds"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-pair/f64-accumulate+f64-polish", "data": "synthetic",
-            "config": {"workload": "batch_fire_512_d3-6_N256-8192_bidisperse",
-                       "jobs": len(specs), "atoms": atoms, "lanes_by_d": lanes[3:7],
-                       "autotuned": bool(args.autotune)},
-            "converged": conv, "stopped_at_max_iter": len(specs) - conv, "max_iter": args.max_iter,
-            "max_fmax_converged": fmax, "fire_iterations_total": iters,
-            "fp64_sequential": {"value": fp64_value, "unit": "converged jobs/s", "jobs": len(sample),
-                                "converged": fp64_conv,
-                                "sample": "first %d jobs, one System(FP64).fire() each" % len(sample)},
-            "speedup_vs_fp64_sequential": value / fp64_value}
+            "config": {"workload": rec["workload"], "jobs": rec["jobs"], "atoms": rec["atoms"],
+                       "max_iter": rec["max_iter"]},
+            "mixed": rec["mixed"], "fp64": rec["fp64"], "speedup_vs_fp64": rec["speedup_vs_fp64"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -644,9 +775,6 @@ def main():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per atom (0: library default)")
     ap.add_argument("--jobs", type=int, default=512, help="batched workload: number of jobs")
-    ap.add_argument("--fp64-sample", type=int, default=16,
-                    help="batched workload: jobs of the sequential FP64 comparison")
-    ap.add_argument("--autotune", type=int, default=1, help="batched workload: run the autotuner")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="serving workload: seconds of Poisson arrivals")
     ap.add_argument("--serve-time-limit", type=float, default=300.0,
@@ -655,7 +783,7 @@ def main():
                     help="serving workload: steps / FIRE iterations per job per launch")
     ap.add_argument("--pool-gb", type=int, default=2,
                     help="serving workload: batched-engine device pool (GiB)")
-    ap.add_argument("--policy", default="fifo", choices=["fifo", "sjf"],
+    ap.add_argument("--policy", default="sjf", choices=["fifo", "sjf"],
                     help="serving workload: admission order of waiting systems")
     ap.add_argument("--slots", type=int, default=16,
                     help="serving workload: concurrent system jobs")
@@ -671,6 +799,8 @@ def main():
     ap.add_argument("--swap-sweeps", type=int, default=100, help="sweep workload: SWAP sweeps")
     ap.add_argument("--sweep-max-iter", type=int, default=200000,
                     help="sweep workload: FIRE iteration limit")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: skip the C1-L, batched and serving sub-records")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels one by one instead of CUDA graphs (for ncu)")
     args = ap.parse_args()

@@ -51,27 +51,32 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hdmd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (gcc, -O2, no FMA contraction) into oracle/_build."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, no FMA contraction) into oracle/_build.
+    openmp=True builds the threaded variant used only to time the oracle on
+    all host cores (the tests use the serial build)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp.%d" % os.getpid()
+    so = _SO_OMP if openmp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + ".tmp.%d" % os.getpid()
         subprocess.check_call(
-            ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+            ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared"]
+            + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, so)
+    return so
 
 
-def _load():
-    global _lib
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            lib = C.CDLL(build())
+        if (_lib_omp if openmp else _lib) is None:
+            lib = C.CDLL(build(openmp=openmp))
             i64, i32, dbl, vp = C.c_int64, C.c_int, C.c_double, C.c_void_p
             lib.orc_sphere_volume.restype = dbl
             lib.orc_sphere_volume.argtypes = [i32, dbl]
@@ -122,8 +127,19 @@ def _load():
             lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
             lib.orc_swap_draw.restype = None
             lib.orc_swap_draw.argtypes = [C.c_uint64, i64, i64, i64, vp, vp]
-            _lib = lib
-    return _lib
+            lib.orc_set_threads.restype = i32
+            lib.orc_set_threads.argtypes = [i32]
+            if openmp:
+                _lib_omp = lib
+            else:
+                _lib = lib
+    return _lib_omp if openmp else _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the OpenMP build for later calls with threads > 1; returns
+    the count it will use."""
+    return int(_load(openmp=True).orc_set_threads(int(n)))
 
 
 def _p(a):
@@ -305,11 +321,12 @@ def kinetic(v, mass=None):
 
 # --------------------------------------------------------------- integrators
 def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None, F=None,
-             T_target=0.0, tau=0.0, rule="exact", n_bet=1, step=0):
+             T_target=0.0, tau=0.0, rule="exact", n_bet=1, step=0, openmp=False):
     """Velocity Verlet on copies (NVE, or NVT with the Berendsen factor
     when tau > 0), lists rebuilt by the exact rule or the paper's (checked
     every n_bet steps, step = steps already counted); returns dict(x, v, img,
-    F, E, W, K, builds, step)."""
+    F, E, W, K, builds, step).  openmp=True runs the threaded build (for
+    timing; its E and W may differ from the serial build's in rounding)."""
     x = _f64(x).copy()
     v = _f64(v).copy()
     N, d = x.shape
@@ -320,7 +337,7 @@ def md_steps(x, v, sigma, L, nsteps, dt, skin=0.3, eps=1.0, mass=None, img=None,
     F = np.zeros_like(x) if F is None else _f64(F).copy()
     th = np.zeros(3)
     stp = np.array([int(step)], dtype=np.int64)
-    b = _load().orc_md_steps(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
+    b = _load(openmp).orc_md_steps(d, N, L, _p(x), _p(v), _p(img), _p(sigma), _p(m), eps, skin,
                              dt, int(nsteps), _p(F), int(have_F), _p(th), float(T_target),
                              float(tau), {"exact": 0, "paper": 1}[rule], int(n_bet), _p(stp))
     return dict(x=x, v=v, img=img, F=F, E=th[0], W=th[1], K=th[2], builds=int(b),

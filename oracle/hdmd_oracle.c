@@ -34,11 +34,33 @@
  * Readings of points the paper leaves open are stated at each function.
  * Positions are row-major x[i*d + k] with every coordinate in [-L/2, L/2).
  * Build with -ffp-contract=off so that x86 and Arm give the same bits.
+ *
+ * The tests use the serial build.  A second build with -fopenmp, used only
+ * to time the oracle on all host cores, runs the per-atom loops (forces over
+ * the lists, kicks and drift, the trigger) and the per-subcell loop of the
+ * list build in parallel, as the paper's OpenMP code does (Sec. II); its
+ * energy and virial sums may then differ from the serial ones in rounding.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP build (1 in the serial build); returns the count
+ * the build will use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define ORC_MAXD 16
 
@@ -221,6 +243,9 @@ int64_t orc_neighbors_cells(int d, int64_t N, double L, const double *x,
     int64_t nstencil = 1;
     for (int k = 0; k < d; ++k) nstencil *= 3;
 
+    /* one subcell per iteration; atom i's list is written only by the
+     * iteration of its own subcell */
+#pragma omp parallel for schedule(dynamic, 4)
     for (int64_t I = 0; I < ncells; ++I) {
         int C[ORC_MAXD];
         int64_t rem = I;
@@ -256,8 +281,9 @@ int64_t orc_neighbors_cells(int d, int64_t N, double L, const double *x,
 
     int64_t tot = 0;
     int overflow = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) qsort(lst[i], (size_t)len[i], sizeof(int32_t), cmp_i32);
     for (int64_t i = 0; i < N; ++i) {
-        qsort(lst[i], (size_t)len[i], sizeof(int32_t), cmp_i32);
         counts[i] = len[i];
         if (idx) {
             if (tot + len[i] > cap) overflow = 1;
@@ -387,8 +413,12 @@ void orc_forces(int d, int64_t N, double L, const double *x, const double *sigma
             }
         }
     } else {
-        int64_t off = 0;
+        int64_t *first = malloc(sizeof(int64_t) * (size_t)(N + 1));
+        first[0] = 0;
+        for (int64_t i = 0; i < N; ++i) first[i + 1] = first[i] + counts[i];
+#pragma omp parallel for reduction(+ : e, w) schedule(static)
         for (int64_t i = 0; i < N; ++i) {
+            const int64_t off = first[i];
             for (int32_t a = 0; a < counts[i]; ++a) {
                 int64_t j = idx[off + a];
                 double dx[ORC_MAXD], r2 = 0.0;
@@ -403,8 +433,8 @@ void orc_forces(int d, int64_t N, double L, const double *x, const double *sigma
                 e += 0.5 * u;
                 w += 0.5 * fr * r2;
             }
-            off += counts[i];
         }
+        free(first);
     }
     *E = e;
     *W = w;
@@ -492,6 +522,7 @@ static int vl_needs_rebuild(const orc_vl *vl, int d, int64_t N, double L,
                             const double *x, double skin)
 {
     double dmax2 = 0.0;
+#pragma omp parallel for reduction(max : dmax2) schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         double s = 0.0;
         for (int k = 0; k < d; ++k) {
@@ -569,6 +600,7 @@ int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *
     vl_build(&vl, d, N, L, x, sigma, skin);
     if (!have_F) orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
     for (int64_t step = 0; step < nsteps; ++step) {
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             double m = mass ? mass[i] : 1.0;
             for (int k = 0; k < d; ++k) {
@@ -585,6 +617,7 @@ int64_t orc_md_steps(int d, int64_t N, double L, double *x, double *v, int32_t *
             vl_build(&vl, d, N, L, x, sigma, skin);
         }
         orc_forces(d, N, L, x, sigma, eps, vl.counts, vl.idx, F, &E, &W);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             double m = mass ? mass[i] : 1.0;
             for (int k = 0; k < d; ++k) v[i * d + k] += 0.5 * dt * F[i * d + k] / m;

@@ -227,6 +227,15 @@ def get_state(h, N, d, x=True, v=True, img=True, f=False, sigma=False):
     return out
 
 
+def get_state_into(h, x_out, v_out=None):
+    """Positions (and velocities) copied into caller arrays of shape (N, d),
+    float64, C-contiguous (pinned host memory makes the copy direct)."""
+    for a in (x_out, v_out):
+        if a is not None and (a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]):
+            raise ValueError("output arrays must be C-contiguous float64")
+    _check(lib().get_state(h, _p(x_out), _p(v_out), None, None, None), h)
+
+
 def build_neighbors(h, force=True):
     r = C.c_int(0)
     _check(lib().build_neighbors(h, 1 if force else 0, C.byref(r)), h)
@@ -367,6 +376,9 @@ class System:
 
     def state(self, **kw):
         return get_state(self.h, self.N, self.d, **kw)
+
+    def state_into(self, x_out, v_out=None):
+        get_state_into(self.h, x_out, v_out)
 
     def build_neighbors(self, force=True):
         return build_neighbors(self.h, force)

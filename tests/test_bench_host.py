@@ -4,6 +4,7 @@ and the measured-peak lookup."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
@@ -94,3 +95,29 @@ def test_reference_arm_prints_one_contract_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"] == bench.WORKLOAD
+
+
+def test_algorithmic_bytes_follow_the_stated_formula():
+    """Bytes per atom-step of the fused force + VV kernel: 4 Z (list) + 4
+    (length) + 4 (diameter) + 16 d (x r/w) + 16 d (v r/w) + 2 b_F d (F w/r):
+    at d = 6, Z = 17.5 that is 318 B in mixed precision (b_F = 4) and 366 B
+    in FP64 (b_F = 8)."""
+    assert bench.alg_bytes_per_atom_step(6, 17.5, 4) == pytest.approx(318.0)
+    assert bench.alg_bytes_per_atom_step(6, 17.5, 8) == pytest.approx(366.0)
+    # the design's own count is larger: 8-byte entries and three FP32 rows
+    assert bench.design_bytes_per_atom_step(6, 17.5) > bench.alg_bytes_per_atom_step(6, 17.5, 4)
+
+
+def test_threaded_oracle_gives_the_serial_trajectory():
+    """The OpenMP build of the oracle (timing only) parallelises per-atom and
+    per-subcell loops: the positions and velocities it returns equal the
+    serial build's bit for bit (only the E and W sums may round differently)."""
+    import oracle
+    from paper_2112_12271_gb300 import workloads as W
+    s = W.make_system(4, 700, phi=0.4, dist="poly", T=0.05, seed=3)
+    a = oracle.md_steps(s.x, s.v, s.sigma, s.L, 60, 0.005)
+    oracle.set_threads(4)
+    b = oracle.md_steps(s.x, s.v, s.sigma, s.L, 60, 0.005, openmp=True)
+    assert a["builds"] == b["builds"] >= 2
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+    assert b["E"] == pytest.approx(a["E"], rel=1e-12)
