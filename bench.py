@@ -408,7 +408,7 @@ def run_gpu(args):
         B.build()
 
     from paper_2112_12271_gb300 import replicas
-    s = W.c1_poly_d6(seed=replicas.replica_seed(rank), N=WORKLOADS[args.workload])
+    s = W.c1_poly_d6(seed=replicas.replica_seed(rank), N=args.atoms or WORKLOADS[args.workload])
     md_per_step = args.md_per_step
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -770,6 +770,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
     ap.add_argument("--md-per-step", type=int, default=MD_PER_STEP)
+    ap.add_argument("--atoms", type=int, default=0,
+                    help="c1/c1l workloads: atoms at the same density (0: the workload's N)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")

@@ -126,6 +126,8 @@ typedef struct {
     int precision;             /* hdmd_precision */
     int graphs;                /* 1 if CUDA graphs with conditional nodes are used */
     int64_t device_bytes;      /* device memory held by the system */
+    int resident;              /* blocks of the resident MD kernel that md_steps
+                                  would launch now (0: one kernel per step) */
 } hdmd_info;
 
 /* Device bytes that create_system would allocate for these arguments (the
@@ -288,6 +290,16 @@ hdmd_status swap_sweep(hdmd_system *sys, int nsweeps, double T, double p,
  * list build, which this call forces. */
 hdmd_status get_info(hdmd_system *sys, hdmd_info *info);
 hdmd_status set_tuning(hdmd_system *sys, int lanes_per_atom, int use_graphs);
+
+/* Resident MD (on = 1, the default): in mixed precision with the exact
+ * rebuild rule, md_steps runs the steps between list builds (Sec. II.C) in
+ * one cooperative launch whose blocks keep their atoms' state and lists in
+ * shared memory and exchange positions through L2 each step; it applies
+ * when the per-atom state fits in shared memory (about 10^5 atoms at d = 6
+ * on GB300).  The trajectory is the same, bit for bit in NVE, as with
+ * on = 0 (one kernel launch per step).  A block that waits too long for the
+ * others makes md_steps return HDMD_E_TIMEOUT. */
+hdmd_status set_resident(hdmd_system *sys, int on);
 
 /* Benchmark support, not part of the method: average device time in
  * milliseconds of single kernels on the current state, each launch timed

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["kernels_bin.cu", "kernels_nbr.cu", "kernels_force.cu", "kernels_swap.cu",
          "kernels_batch_d2.cu", "kernels_batch_d4.cu", "kernels_batch_d6.cu",
          "kernels_batch_d8.cu", "kernels_batch_d9.cu", "system.cu",
-         "batch.cu", "noalloc.cu", "kernels_obs.cu"]
+         "batch.cu", "noalloc.cu", "kernels_obs.cu", "kernels_resident.cu"]
 
 
 def nvcc() -> str:

@@ -290,6 +290,8 @@ hdmd_status batch_add(hdmd_batch *b, const hdmd_job_spec *spec, const double *di
     dv.Npad = (int)((N + 63) / 64 * 64);
     dv.G = 1 << b->lgG[d];
     dv.lgG = b->lgG[d];
+    dv.idx_mask = 0xFFFFFFFFu;   // jobs keep the index and code arrays
+    dv.pack_sh = 0;
     dv.L = spec->L;
     dv.halfL = 0.5 * spec->L;
     dv.invL = 1.0 / spec->L;

@@ -20,11 +20,33 @@
 //                     ((m / G) * Npad + i) * G + m % G for G lanes per atom
 //                     (G = 1 is plain padded SoA), code packs for each axis
 //                     the subcell offset o in {-1,0,1} of the neighbour as
-//                     2 bits (o + 1), so x_i - x_j = gs_i - gs_j - o Lsc;
+//                     2 bits (o + 1), so x_i - x_j = gs_i - gs_j - o Lsc.
+//                     Packed form (pack_sh > 0, when the bits fit): one
+//                     32-bit word per entry, the neighbour's index in the
+//                     low pack_sh bits and above them its stencil position
+//                     s = sum_k (o_k + 1) 3^k; code is then unused;
 //   cell_*            counting-sort scratch of the binning.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+// Streaming (evict-first) loads and stores for the per-atom data a step reads
+// and writes once; HDMD_STREAM_HINTS=0 builds them as plain accesses.
+#ifndef HDMD_STREAM_HINTS
+#define HDMD_STREAM_HINTS 0
+#endif
+#if HDMD_STREAM_HINTS
+#define HDMD_LDS(p) __ldcs(p)
+#define HDMD_STS(p, v) __stcs((p), (v))
+#else
+#define HDMD_LDS(p) (*(p))
+#define HDMD_STS(p, v) (*(p) = (v))
+#endif
+// Packed one-word list entries where the bits fit; HDMD_PACK_LISTS=0 keeps
+// the index and code arrays for every system.
+#ifndef HDMD_PACK_LISTS
+#define HDMD_PACK_LISTS 1
+#endif
 
 namespace hdmd {
 
@@ -35,6 +57,8 @@ constexpr int kNRed = 16;          // reduction slots per block
 #endif
 constexpr int kStepNT = HDMD_STEP_NT;   // threads per block of the force / update kernels
 constexpr int kMaxLanes = 32;      // largest lanes-per-atom group
+constexpr int kResNT = 1024;       // threads per block of the resident MD kernel
+constexpr int kResMaxGrid = 1024;  // most blocks of the resident MD kernel
 
 // reduction slots
 enum Red {
@@ -66,7 +90,7 @@ enum FireSlot {
 enum FireStatus { FIRE_RUNNING = 0, FIRE_CONVERGED = 1, FIRE_MAXITER = 2, FIRE_NEGFAIL = 3,
                   FIRE_SWITCH = 4 };
 
-enum ErrBits { ERR_OVERFLOW = 1, ERR_LOST = 2, ERR_BADARG = 4 };
+enum ErrBits { ERR_OVERFLOW = 1, ERR_LOST = 2, ERR_BADARG = 4, ERR_TIMEOUT = 8 };
 
 struct Flags {
     unsigned int counter;    // last-block-done ticket
@@ -81,6 +105,9 @@ struct Flags {
     long long md_step;       // MD steps since the rebuild rule was set
     double nvt_lambda;       // Berendsen factor for the next second kick
     double nvt_T;            // kinetic temperature it was computed from
+    long long res_left;      // MD steps left for the resident kernel in this call
+    unsigned int res_tick;   // steps the resident kernel has ever run (step words)
+    int pad2;
     double fire[FS_COUNT];
 };
 
@@ -114,6 +141,8 @@ struct Dev {
     // lists
     int32_t *nnbr, *nbr;
     uint32_t *code;
+    uint32_t idx_mask;   // index bits of an entry (every bit without packing)
+    int pack_sh;         // > 0: packed entries, stencil position above bit pack_sh
     // reductions
     double *partials, *red;  // partials: [kNRed][maxblocks]
     int maxblocks;
@@ -134,6 +163,126 @@ template <int D> struct Rows {
 };
 
 __host__ __device__ inline int pow_int(int b, int e) { int r = 1; for (int k = 0; k < e; ++k) r *= b; return r; }
+
+// bits of a stencil position s < 3^d, ceil(log2(3^d))
+__host__ __device__ constexpr int stencil_bits(int d) {
+    return d <= 0 ? 0 : (d == 1 ? 2 : (d == 2 ? 4 : (d == 3 ? 5 : (d == 4 ? 7 : (d == 5 ? 8 :
+           (d == 6 ? 10 : (d == 7 ? 12 : (d == 8 ? 13 : (d == 9 ? 15 : 16)))))))));
+}
+
+// stencil position of a 2-bit-per-axis offset code: s = sum_k c_k 3^k,
+// c_k = o_k + 1 the 2-bit field of axis k
+template <int D>
+__device__ __forceinline__ uint32_t code_to_stencil(uint32_t code) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) s = s * 3u + ((code >> (2 * k)) & 3u);
+    return s;
+}
+
+// the 2-bit-per-axis offset code of a stencil position (inverse of
+// code_to_stencil)
+template <int D>
+__device__ __forceinline__ uint32_t stencil_to_code(uint32_t s) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        c |= (s % 3u) << (2 * k);
+        s /= 3u;
+    }
+    return c;
+}
+
+__host__ __device__ constexpr int pow3(int d) { return d <= 0 ? 1 : 3 * pow3(d - 1); }
+
+// Conversions between IEEE-754 binary32 and binary64 written on the bit
+// fields (sign, biased exponent, significand), so that they run on the
+// integer pipe instead of the narrow FP64 pipe of this GPU.  Both follow the
+// standard's definitions: binary32 -> binary64 is exact; binary64 -> binary32
+// rounds to nearest, ties to even, with overflow to infinity and gradual
+// underflow to subnormals; NaN stays NaN.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    uint32_t hi, lo;
+    if (e != 0u && e != 0xffu) {               // normal: rebias 127 -> 1023
+        hi = sign | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (e == 0xffu) {                   // infinity, NaN
+        hi = sign | 0x7ff00000u | (m >> 3);
+        lo = m << 29;
+    } else if (m == 0u) {                      // signed zero
+        hi = sign;
+        lo = 0u;
+    } else {                                   // subnormal: normalise
+        const int k = __clz(m) - 8;            // shifts that bring bit 23 up
+        const uint32_t mn = (m << k) & 0x7fffffu;
+        hi = sign | ((uint32_t)(897 - k) << 20) | (mn >> 3);
+        lo = mn << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the kept 23 bits
+    const uint32_t rest = lo & 0x1fffffffu;                      // the 29 dropped bits
+    if (e == 0x7ff)                                              // infinity, NaN
+        return __uint_as_float(sign | 0x7f800000u | m23 | ((m23 | rest) ? 0x400000u : 0u));
+    const int ef = e - 896;
+    if (ef >= 1) {
+        if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+        uint32_t r = sign | ((uint32_t)ef << 23) | m23;
+        r += (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+        return __uint_as_float(r);   // a carry into the exponent is the rounded value
+    }
+    // binary32 subnormal or zero: significand with its leading 1, shifted
+    if (e == 0) return __uint_as_float(sign);   // binary64 zero or subnormal: below 2^-1022
+    const uint64_t M = ((uint64_t)(0x100000u | (hi & 0xfffffu)) << 32) | lo;   // 53 bits
+    const int sh = 926 - e;                     // >= 30
+    if (sh >= 64) return __uint_as_float(sign);
+    const uint64_t q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    const uint32_t r = (uint32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
+    return __uint_as_float(sign | r);
+}
+
+#ifndef HDMD_INT_CVT
+#define HDMD_INT_CVT 1
+#endif
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float f) {
+#if HDMD_INT_CVT
+    return f32_to_f64(f);
+#else
+    return (double)f;
+#endif
+}
+__device__ __forceinline__ float to_f32(double x) {
+#if HDMD_INT_CVT
+    return f64_to_f32(x);
+#else
+    return (float)x;
+#endif
+}
+
+// Largest d whose packed entries are decoded through a shared-memory table
+// of 3^d codes (2.9 KB at d = 6); larger d keep the two arrays.
+constexpr int kMaxPackD = 6;
+
+// o_k = c_k - 1 of axis k as a float, c_k the 2-bit field of the code:
+// 2^23 + 2^22 + c_k has c_k in its last significand bits, and subtracting
+// 2^23 + 2^22 + 1 leaves c_k - 1 exactly (no integer-to-float conversion)
+__device__ __forceinline__ float code_offset(uint32_t code, int k) {
+    return __uint_as_float(0x4B400000u | ((code >> (2 * k)) & 3u)) - 12582913.0f;
+}
+
+// the list entry written for neighbour j with offset code `code`
+template <int D>
+__device__ __forceinline__ uint32_t pack_entry(const Dev &dv, int j, uint32_t code) {
+    return (uint32_t)j | (code_to_stencil<D>(code) << dv.pack_sh);
+}
 
 // entry m of atom i (G = 1 << lgG lanes per atom)
 __device__ __forceinline__ int64_t list_pos(int m, int i, int Npad, int lgG) {

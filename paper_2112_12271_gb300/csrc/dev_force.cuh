@@ -48,13 +48,55 @@ __device__ __forceinline__ T eps_pair(T eps, T hi, T hj, int scale) {
     return eps * q;
 }
 
-template <int D, bool FP64P, typename FT, int LAW = 0>
+// One pair's contribution in FP32 arithmetic: dx = x_i - x_j (minimum
+// image), r2 = |dx|^2, radii hi, hj (s = hi + hj is the contact distance);
+// adds the force on i to f, U to e and r.f to w when r < s.
+template <int D, typename FT, int LAW>
+__device__ __forceinline__ void pair_term_f32(const Dev &dv, const float (&dx)[D], float r2, float hi,
+                                              float hj, float eps, float ma, int scale, FT (&f)[D],
+                                              FT &e, FT &w) {
+    const float s = hi + hj;
+    if (r2 < s * s) {
+        // coincident atoms: no force (direction undefined), U(0)
+        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        const float r = r2 * rinv;
+        const float ee = eps_pair<D, float>(eps, hi, hj, scale);
+        if constexpr (LAW == 2) {
+            const float q = powi(s * rinv, dv.mie_n);
+            const float fr = 2.f * (float)dv.mie_n * ee * (q * q - q) * rinv * rinv;
+#pragma unroll
+            for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+            e = (FT)fmaf(ee * (q - 1.f), q - 1.f, (float)e);
+            w = (FT)fmaf(fr, r2, (float)w);
+        } else if constexpr (LAW == 0) {
+            const float inv_s = __fdividef(1.f, s);   // approximate: within 2 ulp
+            const float gg = fmaf(-r, inv_s, 1.f);
+            const float fr = ee * inv_s * gg * rinv;
+#pragma unroll
+            for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+            e = (FT)fmaf(0.5f * ee * gg, gg, (float)e);
+            w = (FT)fmaf(fr, r2, (float)w);
+        } else {
+            const float m = expm1f(-ma * (r - s));
+            const float fr = 2.f * ma * ee * (m + 1.f) * m * rinv;
+#pragma unroll
+            for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
+            e = (FT)fmaf(ee * m, m, (float)e);
+            w = (FT)fmaf(fr, r2, (float)w);
+        }
+    }
+}
+
+// PACK: one-word entries, the offset code looked up in stab (a shared-memory
+// table of the 3^D codes by stencil position)
+template <int D, bool FP64P, typename FT, int LAW = 0, bool PACK = false>
 __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG, int in_buf,
-                                            FT (&f)[D], FT &e, FT &w) {
+                                            FT (&f)[D], FT &e, FT &w,
+                                            const uint32_t *stab = nullptr) {
     constexpr int RF = Rows<D>::RF, RD = Rows<D>::RD;
     const int G = 1 << lgG;
     const int Np = dv.Npad;
-    const int nn = dv.nnbr[i];
+    const int nn = HDMD_LDS(dv.nnbr + i);
     if (FP64P) {
         const double *ri = dv.gd[in_buf] + (size_t)i * RD;
         double xi[D];
@@ -64,7 +106,7 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
         const int64_t lstride = (int64_t)Np << lgG;
         int64_t pos = ((int64_t)i << lgG) + g;
         for (int m = g; m < nn; m += G, pos += lstride) {
-            const int j = dv.nbr[pos];
+            const int j = (int)((uint32_t)dv.nbr[pos] & dv.idx_mask);
             const double *rj = dv.gd[in_buf] + (size_t)j * RD;
             double dx[D], r2 = 0.0;
 #pragma unroll
@@ -113,30 +155,33 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
         int64_t pos0 = ((int64_t)i << lgG) + g;
         // the list entries of the next chunk are loaded one chunk ahead (the
         // first chunk before the list length is known: any slot below the
-        // capacity may be read; the length decides which entries count)
-        int jn[U];
+        // capacity may be read; the length decides which entries count).
+        // Entries and codes are read once per step: streaming loads, so that
+        // they do not push the neighbour rows out of L2.
+        const uint32_t *nb = reinterpret_cast<const uint32_t *>(dv.nbr);
+        uint32_t jn[U];
         uint32_t cn[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool in = g + u * G < dv.cap;
-            jn[u] = in ? dv.nbr[pos0 + u * lstride] : -1;
-            cn[u] = in ? dv.code[pos0 + u * lstride] : 0u;
+            jn[u] = in ? HDMD_LDS(nb + pos0 + u * lstride) : 0u;
+            cn[u] = (!PACK && in) ? HDMD_LDS(dv.code + pos0 + u * lstride) : 0u;
         }
         for (int m0 = g; m0 < nn; m0 += U * G, pos0 += U * lstride) {
             int jv[U];
             uint32_t cv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                jv[u] = m0 + u * G < nn ? jn[u] : -1;
-                cv[u] = cn[u];
+                jv[u] = m0 + u * G < nn ? (int)(PACK ? jn[u] & dv.idx_mask : jn[u]) : -1;
+                cv[u] = PACK ? stab[jv[u] >= 0 ? jn[u] >> dv.pack_sh : 0u] : cn[u];
             }
             if (m0 + U * G < nn) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const bool ok = m0 + (U + u) * G < nn;
                     const int64_t pos = pos0 + (U + u) * lstride;
-                    jn[u] = ok ? dv.nbr[pos] : -1;
-                    cn[u] = ok ? dv.code[pos] : 0u;
+                    jn[u] = ok ? HDMD_LDS(nb + pos) : 0u;
+                    cn[u] = (!PACK && ok) ? HDMD_LDS(dv.code + pos) : 0u;
                 }
             }
             float rj[U][RF];
@@ -158,41 +203,12 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
                 float dx[D], r2 = 0.f;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const float o = (float)((int)((code >> (2 * k)) & 3u) - 1);
+                    const float o = code_offset(code, k);
                     const float t = fmaf(-o, Lsc, xi[k] - rj[u][k]);
                     dx[k] = t;
                     r2 = fmaf(t, t, r2);
                 }
-                const float s = hi + rj[u][D];
-                if (r2 < s * s) {
-                    // coincident atoms: no force (direction undefined), U(0)
-                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                    const float r = r2 * rinv;
-                    const float ee = eps_pair<D, float>(eps, hi, rj[u][D], scale);
-                    if constexpr (LAW == 2) {
-                        const float q = powi(s * rinv, dv.mie_n);
-                        const float fr = 2.f * (float)dv.mie_n * ee * (q * q - q) * rinv * rinv;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
-                        e = (FT)fmaf(ee * (q - 1.f), q - 1.f, (float)e);
-                        w = (FT)fmaf(fr, r2, (float)w);
-                    } else if constexpr (LAW == 0) {
-                        const float inv_s = __frcp_rn(s);
-                        const float gg = fmaf(-r, inv_s, 1.f);
-                        const float fr = ee * inv_s * gg * rinv;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
-                        e = (FT)fmaf(0.5f * ee * gg, gg, (float)e);
-                        w = (FT)fmaf(fr, r2, (float)w);
-                    } else {
-                        const float m = expm1f(-ma * (r - s));
-                        const float fr = 2.f * ma * ee * (m + 1.f) * m * rinv;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) f[k] = (FT)fmaf(fr, dx[k], (float)f[k]);
-                        e = (FT)fmaf(ee * m, m, (float)e);
-                        w = (FT)fmaf(fr, r2, (float)w);
-                    }
-                }
+                pair_term_f32<D, FT, LAW>(dv, dx, r2, hi, rj[u][D], eps, ma, scale, f, e, w);
             }
         }
     }

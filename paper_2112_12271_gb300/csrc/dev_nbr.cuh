@@ -227,8 +227,12 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                             const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
                             if (idx < dv.cap) {
                                 const int64_t pos = list_pos(idx, h0 + h, dv.Npad, dv.lgG);
-                                dv.nbr[pos] = j;
-                                dv.code[pos] = wcode;
+                                if (dv.pack_sh) {
+                                    dv.nbr[pos] = (int32_t)pack_entry<D>(dv, j, wcode);
+                                } else {
+                                    dv.nbr[pos] = j;
+                                    dv.code[pos] = wcode;
+                                }
                             }
                         }
                         cnt[h] += __popc(m);
@@ -295,8 +299,12 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
                             const int idx = cnt[h] + __popc(m & ((1u << lane) - 1u));
                             if (idx < dv.cap) {
                                 const int64_t pos = list_pos(idx, i, dv.Npad, dv.lgG);
-                                dv.nbr[pos] = j;
-                                dv.code[pos] = code;
+                                if (dv.pack_sh) {
+                                    dv.nbr[pos] = (int32_t)pack_entry<D>(dv, j, code);
+                                } else {
+                                    dv.nbr[pos] = j;
+                                    dv.code[pos] = code;
+                                }
                             }
                         }
                         cnt[h] += __popc(m);

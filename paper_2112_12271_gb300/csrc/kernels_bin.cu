@@ -126,7 +126,7 @@ __global__ void k_list_export(Dev dv, int32_t *counts, int32_t *idx, const int64
     if (counts) counts[c] = n;
     if (idx) {
         int64_t off = offsets[c];
-        for (int m = 0; m < n; ++m) idx[off + m] = dv.id[dv.nbr[list_pos(m, s, dv.Npad, dv.lgG)]];
+        for (int m = 0; m < n; ++m) idx[off + m] = dv.id[(uint32_t)dv.nbr[list_pos(m, s, dv.Npad, dv.lgG)] & dv.idx_mask];
     }
 }
 

@@ -132,6 +132,19 @@ __device__ __forceinline__ void trigger_fold(const Dev &dv, float blk_max_d2, bo
     }
 }
 
+// pair forces of atom i with the list form of the system: packed entries
+// (FP32 pair path only; the FP64 path takes the index bits alone)
+template <int D, bool FP64P, typename FT, int LAW>
+__device__ __forceinline__ void pair_forces_of(const Dev &dv, int i, int g, int lgG, int in_buf,
+                                               FT (&f)[D], FT &e, FT &w, const uint32_t *stab) {
+    if constexpr (FP64P || D > kMaxPackD) {
+        pair_forces<D, FP64P, FT, LAW, false>(dv, i, g, lgG, in_buf, f, e, w);
+    } else {
+        if (dv.pack_sh) pair_forces<D, false, FT, LAW, true>(dv, i, g, lgG, in_buf, f, e, w, stab);
+        else pair_forces<D, false, FT, LAW, false>(dv, i, g, lgG, in_buf, f, e, w);
+    }
+}
+
 // The MD / force kernel.  Phase A: G lanes per atom accumulate the pair
 // forces over the list and meet through xor shuffles; lane 0 parks the force
 // in shared memory.  Phase B: the block's (atom, axis) items are spread over
@@ -148,7 +161,13 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
     __shared__ float sDl[NT * D];   // (float) dlt of the drift, summed per atom in axis order
     __shared__ float sPos[FP64P ? 1 : NT * RF];
     __shared__ int sBad;
+    // offset codes by stencil position, for packed list entries
+    __shared__ uint32_t sStab[(!FP64P && D <= kMaxPackD) ? pow3(D) : 1];
     if (cfg.fire_red && dv.flags->fire[FS_STATUS] != (double)FIRE_RUNNING) return;  // loop ended
+    if (!FP64P && D <= kMaxPackD && dv.pack_sh && cfg.compute_force) {
+        for (int t = threadIdx.x; t < pow3(D); t += NT) sStab[t] = stencil_to_code<D>((uint32_t)t);
+        __syncthreads();
+    }
     const int G = dv.G, lgG = dv.lgG, APB = NT >> lgG;
     const int lgAPB = __ffs(NT) - 1 - lgG;   // APB is a power of two
     const int al = threadIdx.x >> lgG, g = threadIdx.x & (G - 1);
@@ -164,9 +183,9 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
         for (int k = 0; k < D; ++k) f[k] = 0;
         FT e = 0, w = 0;
         if (valid) {
-            if (dv.law == 1) pair_forces<D, FP64P, FT, 1>(dv, i, g, lgG, cfg.in_buf, f, e, w);
-            else if (dv.law == 2) pair_forces<D, FP64P, FT, 2>(dv, i, g, lgG, cfg.in_buf, f, e, w);
-            else pair_forces<D, FP64P, FT, 0>(dv, i, g, lgG, cfg.in_buf, f, e, w);
+            if (dv.law == 1) pair_forces_of<D, FP64P, FT, 1>(dv, i, g, lgG, cfg.in_buf, f, e, w, sStab);
+            else if (dv.law == 2) pair_forces_of<D, FP64P, FT, 2>(dv, i, g, lgG, cfg.in_buf, f, e, w, sStab);
+            else pair_forces_of<D, FP64P, FT, 0>(dv, i, g, lgG, cfg.in_buf, f, e, w, sStab);
         }
         for (int o = G >> 1; o > 0; o >>= 1) {
 #pragma unroll
@@ -199,11 +218,14 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
         const int k = t >> lgAPB, a = t & (APB - 1), ii = base + a;
         if (ii >= dv.N) continue;
         const size_t o = (size_t)k * Np + ii;
-        const double F = cfg.compute_force ? (double)sF[a * D + k] : dv.F[o];
+        // v and dlt are read and written once per step: streaming accesses
+        // (evict first), which leave L2 to the neighbour rows
+        const double F = cfg.compute_force ? to_f64(sF[a * D + k]) : dv.F[o];
         if (cfg.store_F) dv.F[o] = F;
         const double im = dv.inv_mass ? dv.inv_mass[ii] : 1.0;
-        const double Fm = dv.inv_mass ? F * im : F;
-        double v = dv.v[o];
+        double Fm = F;
+        if (dv.inv_mass) Fm = F * im;   // a branch: no multiply without masses
+        double v = HDMD_LDS(dv.v + o);
         if (nvt) {
             const double vf = (v + cfg.halfdt * Fm) * lam;
             kin += vf * vf / im;
@@ -220,14 +242,14 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
             acc[R_FN] += F * F;
         }
         if (cfg.kick1_drift) {
-            const double dl = dv.dlt[o] + cfg.dt * v;
-            dv.dlt[o] = dl;
-            const float fl = (float)dl;
+            const double dl = HDMD_LDS(dv.dlt + o) + cfg.dt * v;
+            HDMD_STS(dv.dlt + o, dl);
+            const float fl = to_f32(dl);
             sDl[a * D + k] = fl;
             if (FP64P) dv.gd[cfg.out_buf][(size_t)ii * RD + k] = dv.x0[o] + dl;
-            else sPos[a * RF + k] = dv.gs0[(size_t)ii * RF + k] + fl;
+            else sPos[a * RF + k] = HDMD_LDS(dv.gs0 + (size_t)ii * RF + k) + fl;
         }
-        if (do_kick) dv.v[o] = v;
+        if (do_kick) HDMD_STS(dv.v + o, v);
     }
     if (cfg.thermo || cfg.fire_red) {
         for (int a = threadIdx.x; a < APB; a += NT) {
@@ -252,7 +274,7 @@ __global__ void __launch_bounds__(NT, HDMD_STEP_MIN_BLOCKS) k_step(Dev dv, StepC
             for (int t = threadIdx.x; t < APB * RF; t += NT) {
                 const int a = t / RF, c = t - a * RF, ii = base + a;
                 if (ii >= dv.N) continue;
-                go[(size_t)ii * RF + c] = c < D ? sPos[a * RF + c] : dv.gs0[(size_t)ii * RF + c];
+                go[(size_t)ii * RF + c] = c < D ? sPos[a * RF + c] : HDMD_LDS(dv.gs0 + (size_t)ii * RF + c);
             }
         } else {
             for (int a = threadIdx.x; a < APB; a += NT)

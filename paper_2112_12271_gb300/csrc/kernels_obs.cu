@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(NT) k_observe(Dev dv, const double *ref, doubl
             const int nn = dv.nnbr[s];
             int z = 0;
             for (int m = 0; m < nn; ++m) {
-                const int j = dv.nbr[list_pos(m, s, dv.Npad, dv.lgG)];
+                const int j = (int)((uint32_t)dv.nbr[list_pos(m, s, dv.Npad, dv.lgG)] & dv.idx_mask);
                 double r2 = 0.0;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {

@@ -76,6 +76,26 @@ void launch_rows(const Dev &dv, int buf, int want32, int want64, cudaStream_t s)
 void launch_fire_update(const Dev &dv, int write_fp64_rows, unsigned long long cond_rebuild,
                         cudaStream_t s);
 
+// ---- kernels_resident.cu
+struct ResCfg {
+    double dt, halfdt;
+    int in_buf;            // rows of the first step (and, on return, of the last)
+    int nvt;               // Berendsen NVT
+    double nvt_rate, nvt_T;
+    int na_cap;            // atoms per block, at most (shared-memory layout)
+    int list_cap;          // list words per block held in shared memory
+    long long spin_limit;  // polls of a step word before ERR_TIMEOUT
+    unsigned long long *sync;   // [2][grid] step words (tick << 32 | max |dlt|^2 bits)
+    double *kin;                // [2][grid] NVT partial sums
+    unsigned long long cond_loop, cond_rebuild;   // graph conditionals (0: none)
+};
+// shared-memory bytes of the per-atom arrays of the resident kernel
+size_t resident_fixed_smem(int d, int na_cap, bool pack);
+cudaError_t launch_md_resident(const Dev &dv, const ResCfg &rc, int grid, size_t smem, cudaStream_t s);
+cudaError_t resident_occupancy(const Dev &dv, size_t smem, int *blocks_per_sm);
+// steps the next resident launches may run (flags->res_left)
+void launch_set_res_left(const Dev &dv, long long nsteps, cudaStream_t s);
+
 // ---- kernels_swap.cu
 struct SwapDev {
     int npairs;

@@ -152,6 +152,11 @@ struct hdmd_system {
     // graphs
     std::map<std::tuple<int, int, int, uint64_t>, GraphEx> md_graphs;  // (kind, len, in_buf, dt bits)
     std::map<int, GraphEx> fire_graphs;                                // fp64 phase -> graph
+    // resident MD kernel (one cooperative launch per list; see kernels_resident.cu)
+    int use_resident = 1;
+    bool res_graph_ok = true;
+    unsigned long long *res_sync = nullptr;   // [2][kResMaxGrid] step words
+    double *res_kin = nullptr;                // [2][kResMaxGrid] NVT partials
     // SWAP buffers (allocated on first use)
     SwapDev sw{};
     int sw_cap_pairs = 0;
@@ -245,19 +250,21 @@ hdmd_status alloc_lists(hdmd_system *sys, int cap) {
     if (sys->code) { pool_free(sys->code, sys->stream); sys->code = nullptr; }
     sys->bytes -= sys->list_bytes;
     const size_t cnt = (size_t)cap * sys->dv.Npad;
+    const bool packed = sys->dv.pack_sh > 0;   // one word per entry: no code array
+    const size_t words = packed ? cnt : 2 * cnt;
     void *a = nullptr, *b = nullptr;
     cudaError_t e1 = pool_alloc(&a, cnt * sizeof(int32_t), sys->stream);
-    cudaError_t e2 = e1 == cudaSuccess ? pool_alloc(&b, cnt * sizeof(uint32_t), sys->stream) : e1;
+    cudaError_t e2 = (e1 == cudaSuccess && !packed) ? pool_alloc(&b, cnt * sizeof(uint32_t), sys->stream) : e1;
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
         if (e1 == cudaSuccess) pool_free(a, sys->stream);
         sys->list_bytes = 0;
         return fail(sys, HDMD_E_NOMEM, "Verlet list allocation of " +
-                                           std::to_string(2 * cnt * 4) + " bytes failed");
+                                           std::to_string(words * 4) + " bytes failed");
     }
     sys->nbr = (int32_t *)a;
     sys->code = (uint32_t *)b;
-    sys->list_bytes = (int64_t)(2 * cnt * 4);
+    sys->list_bytes = (int64_t)(words * 4);
     sys->bytes += sys->list_bytes;
     sys->dv.nbr = sys->nbr;
     sys->dv.code = sys->code;
@@ -318,6 +325,8 @@ hdmd_status check_device_errors(hdmd_system *sys) {
                     "non-finite coordinates or a displacement beyond L/4 since the last list build");
     if (sys->h_flags->error & ERR_OVERFLOW)
         return fail(sys, HDMD_E_NBR_OVERFLOW, "Verlet list capacity exceeded");
+    if (sys->h_flags->error & ERR_TIMEOUT)
+        return fail(sys, HDMD_E_TIMEOUT, "a block of the resident MD kernel gave up waiting for the others");
     return HDMD_OK;
 }
 
@@ -548,6 +557,171 @@ hdmd_status nvt_prepare(hdmd_system *sys, int buf, bool fp64, double dt) {
 
 constexpr int kChunk = 64;
 
+// ----------------------------------------------------------------- resident MD
+// Launch shape of the resident kernel for the current system: grid (at most
+// one block per SM, at least 64 atoms per block), atoms per block and the
+// shared memory, whose remainder after the per-atom arrays holds the lists.
+// False where the path does not apply (FP64 pairs, the paper's rebuild rule,
+// no cooperative launch, or per-atom arrays too large for shared memory):
+// md_steps then launches one kernel per step.
+struct ResPlan {
+    int grid = 0, na_cap = 0, list_cap = 0;
+    size_t smem = 0;
+};
+
+bool resident_plan(hdmd_system *sys, ResPlan *p) {
+    if (!sys->use_resident || sys->prec != HDMD_MIXED || sys->rule != 0) return false;
+    int dev = 0, sms = 0, optin = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!coop) return false;
+    const int64_t N = sys->N;
+    int grid = (int)std::min<int64_t>(std::min(sms, kResMaxGrid), std::max<int64_t>(1, N / 64));
+    const int na_cap = (int)((N + grid - 1) / grid);
+    const bool pack = sys->d <= kMaxPackD && sys->dv.pack_sh > 0;
+    const size_t word = pack ? 4 : 8;
+    const size_t fixed = resident_fixed_smem(sys->d, na_cap, pack);
+    const size_t static_smem = 10 * 1024;   // the kernel's own shared arrays
+    if ((size_t)optin < static_smem + fixed + 16 * word * (size_t)na_cap) return false;
+    const size_t budget = (size_t)optin - static_smem;
+    const size_t list_cap = std::min((budget - fixed) / word, (size_t)na_cap * (size_t)sys->dv.cap);
+    const size_t smem = (fixed + list_cap * word + 15) & ~(size_t)15;
+    int occ = 0;
+    if (resident_occupancy(sys->dv, smem, &occ) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    p->grid = grid;
+    p->na_cap = na_cap;
+    p->list_cap = (int)list_cap;
+    p->smem = smem;
+    return true;
+}
+
+ResCfg resident_cfg(const hdmd_system *sys, const ResPlan &p, int in_buf, double dt) {
+    ResCfg rc;
+    std::memset(&rc, 0, sizeof(rc));
+    rc.dt = dt;
+    rc.halfdt = 0.5 * dt;
+    rc.in_buf = in_buf;
+    if (sys->nvt_tau > 0.0) {
+        rc.nvt = 1;
+        rc.nvt_rate = dt / sys->nvt_tau;
+        rc.nvt_T = sys->nvt_T;
+    }
+    rc.na_cap = p.na_cap;
+    rc.list_cap = p.list_cap;
+    rc.spin_limit = 1 << 21;   // ~0.1-1 s of polling: ERR_TIMEOUT after it
+    rc.sync = sys->res_sync;
+    rc.kin = sys->res_kin;
+    return rc;
+}
+
+// WHILE(steps left) { resident kernel; IF(trigger) list build }
+hdmd_status build_res_graph(hdmd_system *sys, const ResPlan &pl, int in_buf, double dt,
+                            GraphEx *out) {
+    cudaStream_t cs = sys->cap_stream, cs2 = sys->cap_stream2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    hdmd_status st = HDMD_OK;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    cudaGraphConditionalHandle hw = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault);
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd);
+    cudaGraphNode_t node;
+    cudaGraphNodeParams p = {};
+    if (e == cudaSuccess) {
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = hw;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        cudaGraphConditionalHandle hi = 0;
+        e = cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            ResCfg rc = resident_cfg(sys, pl, in_buf, dt);
+            rc.cond_loop = hw;
+            rc.cond_rebuild = hi;
+            e = launch_md_resident(sys->dv, rc, pl.grid, pl.smem, cs2);
+            if (e == cudaSuccess) st = add_if_rebuild(sys, cs2, hi, in_buf, sys->cap_stream3);
+            cudaGraph_t bo = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(cs2, &bo);
+            if (e == cudaSuccess) e = e3;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (st != HDMD_OK || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (st != HDMD_OK) return st;
+        return fail(sys, HDMD_E_CUDA, std::string("resident graph capture: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(sys, HDMD_E_CUDA, std::string("resident graph instantiate: ") + cudaGetErrorString(e));
+    }
+    out->graph = graph;
+    out->exec = ex;
+    return HDMD_OK;
+}
+
+// nsteps middle MD steps (force, both kicks, drift) through the resident
+// kernel, rows in and out of gather buffer in_buf; lists rebuilt whenever the
+// trigger fires
+hdmd_status run_resident(hdmd_system *sys, const ResPlan &pl, int64_t nsteps, int in_buf, double dt) {
+    launch_set_res_left(sys->dv, nsteps, sys->stream);
+    CKL(sys);
+    if (sys->use_graphs && sys->graphs_ok && sys->res_graph_ok) {
+        auto key = std::make_tuple(2, 0, in_buf, dbits(dt));
+        auto it = sys->md_graphs.find(key);
+        if (it == sys->md_graphs.end()) {
+            GraphEx ge;
+            hdmd_status st = build_res_graph(sys, pl, in_buf, dt, &ge);
+            if (st != HDMD_OK) {
+                sys->res_graph_ok = false;   // the eager loop below from now on
+                sys->graph_err = sys->err;
+                g_thread_err.clear();
+                sys->err.clear();
+            } else {
+                it = sys->md_graphs.emplace(key, ge).first;
+            }
+        }
+        if (sys->res_graph_ok) {
+            CK(cudaGraphLaunch(it->second.exec, sys->stream));
+            return HDMD_OK;
+        }
+    }
+    const ResCfg rc = resident_cfg(sys, pl, in_buf, dt);
+    for (;;) {
+        CK(launch_md_resident(sys->dv, rc, pl.grid, pl.smem, sys->stream));
+        launch_rebuild(sys->dv, in_buf, true, sys->stream);
+        CKL(sys);
+        hdmd_status st = read_flags(sys);
+        if (st) return st;
+        if (sys->h_flags->res_left <= 0 || sys->h_flags->error) return HDMD_OK;
+    }
+}
+
 hdmd_status md_once(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *last) {
     hdmd_status st = clear_errors(sys);
     if (st) return st;
@@ -569,11 +743,17 @@ hdmd_status md_once(hdmd_system *sys, int64_t nsteps, double dt, hdmd_thermo *la
         if (st) return st;
     }
     int cur = sys->buf;
+    ResPlan pl;
     if (nsteps > 0) {
         st = run_md_piece(sys, 0, 1, cur, dt);
         if (st) return st;
         cur = 1 - cur;
         int64_t left = nsteps - 1;
+        if (left > 0 && resident_plan(sys, &pl)) {
+            st = run_resident(sys, pl, left, cur, dt);
+            if (st) return st;
+            left = 0;
+        }
         while (left > 0) {
             int len = (int)std::min<int64_t>(left, kChunk);
             st = run_md_piece(sys, 1, len, cur, dt);
@@ -970,8 +1150,17 @@ hdmd_status check_create_args(int d, int64_t N, double L, const double *diameter
     return HDMD_OK;
 }
 
+// Index bits of a list entry when the stencil position fits beside them in
+// one 32-bit word (packed entries), else 0.
+int pack_shift(int d, int64_t Npad) {
+    int sh = 1;
+    while (((int64_t)1 << sh) < Npad) ++sh;
+    return (HDMD_PACK_LISTS && d <= kMaxPackD && stencil_bits(d) + sh <= 32) ? sh : 0;
+}
+
 // Bytes of the arrays create_system allocates, in its order and with the
-// same rounding as dalloc, plus the two list arrays at capacity cap.
+// same rounding as dalloc, plus the list arrays at capacity cap (one word per
+// entry when packed, two otherwise).
 int64_t create_bytes(int d, int64_t N, int64_t ncells, int cap, int G) {
     const size_t Np = (size_t)((N + 63) / 64 * 64), nd = (size_t)d * Np;
     const size_t RF = kRowFloats(d), RD = kRowDoubles(d);
@@ -998,11 +1187,13 @@ int64_t create_bytes(int d, int64_t N, int64_t ncells, int cap, int G) {
     SB(st_i, nd); SB(st_cnt, Np); SB(st_off, Np + 1);
     SB(snap_x0, nd); SB(snap_dlt, nd); SB(snap_v, nd); SB(snap_sig, Np);
     SB(snap_im, Np); SB(snap_img, nd); SB(snap_id, Np);
+    SB(res_sync, 2 * kResMaxGrid); SB(res_kin, 2 * kResMaxGrid);
 #undef FB
 #undef SB
     int64_t c = ((int64_t)(cap + G - 1) / G) * G;
     if (c < G) c = G;
-    b += (int64_t)(sizeof(int32_t) + sizeof(uint32_t)) * c * (int64_t)Np;   // nbr, code
+    const int64_t words = pack_shift(d, (int64_t)Np) ? 1 : 2;   // nbr (and code)
+    b += (int64_t)sizeof(int32_t) * words * c * (int64_t)Np;
     return b;
 }
 
@@ -1050,6 +1241,8 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     dv.Npad = (int)((N + 63) / 64 * 64);
     dv.G = default_lanes(N);
     dv.lgG = __builtin_ctz(dv.G);
+    dv.pack_sh = pack_shift(d, dv.Npad);
+    dv.idx_mask = dv.pack_sh ? (uint32_t)(((uint64_t)1 << dv.pack_sh) - 1) : 0xFFFFFFFFu;
     dv.L = L;
     dv.halfL = 0.5 * L;
     dv.invL = 1.0 / L;
@@ -1097,6 +1290,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     DA2(sys->st_i, nd); DA2(sys->st_cnt, Np); DA2(sys->st_off, Np + 1);
     DA2(sys->snap_x0, nd); DA2(sys->snap_dlt, nd); DA2(sys->snap_v, nd); DA2(sys->snap_sig, Np);
     DA2(sys->snap_im, Np); DA2(sys->snap_img, nd); DA2(sys->snap_id, Np);
+    DA2(sys->res_sync, 2 * kResMaxGrid); DA2(sys->res_kin, 2 * kResMaxGrid);
 #undef DA2
     sys->h_flags = (Flags *)pinned_get();
     sys->h_red = (double *)pinned_get();
@@ -1111,6 +1305,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
         return bail(fail(sys, HDMD_E_CUDA, "stream creation failed"));
     }
     if (cudaMemsetAsync(dv.flags, 0, sizeof(Flags), sys->stream) != cudaSuccess ||
+        cudaMemsetAsync(sys->res_sync, 0, sizeof(unsigned long long) * 2 * kResMaxGrid, sys->stream) != cudaSuccess ||
         cudaMemsetAsync(dv.cell_count, 0, sizeof(int32_t) * dv.ncells, sys->stream) != cudaSuccess ||
         cudaMemsetAsync(dv.nnbr, 0, sizeof(int32_t) * Np, sys->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -1712,6 +1907,14 @@ hdmd_status get_info(hdmd_system *sys, hdmd_info *info) {
     info->precision = sys->prec;
     info->graphs = sys->use_graphs && sys->graphs_ok;
     info->device_bytes = sys->bytes;
+    ResPlan pl;
+    info->resident = resident_plan(sys, &pl) ? pl.grid : 0;
+    return HDMD_OK;
+}
+
+hdmd_status set_resident(hdmd_system *sys, int on) {
+    if (!sys) return fail(nullptr, HDMD_E_INVALID, "null system");
+    sys->use_resident = on ? 1 : 0;
     return HDMD_OK;
 }
 

@@ -69,7 +69,8 @@ class Info(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int64), ("L", C.c_double), ("n_cell", C.c_int),
                 ("n_cells", C.c_int64), ("list_capacity", C.c_int), ("lanes_per_atom", C.c_int),
                 ("max_list_length", C.c_int), ("total_list_entries", C.c_int64),
-                ("precision", C.c_int), ("graphs", C.c_int), ("device_bytes", C.c_int64)]
+                ("precision", C.c_int), ("graphs", C.c_int), ("device_bytes", C.c_int64),
+                ("resident", C.c_int)]
 
 
 class JobSpec(C.Structure):
@@ -125,6 +126,7 @@ def lib():
             "swap_sweep": [vp, i32, dbl, dbl, C.c_uint64, vp, vp, i64, C.POINTER(i64), vp],
             "get_info": [vp, vp],
             "set_tuning": [vp, i32, i32],
+            "set_resident": [vp, i32],
             "destroy_system": [vp],
             "profile_kernels": [vp, i32, dbl, vp],
             "batch_create": [i64, i32, i32, vp, C.POINTER(vp)],
@@ -427,6 +429,10 @@ class System:
 
     def tune(self, lanes_per_atom=0, use_graphs=-1):
         set_tuning(self.h, lanes_per_atom, use_graphs)
+
+    def resident(self, on=True):
+        """Resident MD kernel on or off (see set_resident in hdmd.h)."""
+        _check(lib().set_resident(self.h, 1 if on else 0), self.h)
 
     def profile(self, reps=50, dt=0.005):
         return profile_kernels(self.h, reps, dt)
