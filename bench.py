@@ -260,20 +260,24 @@ def design_bytes_per_atom_step(d, Z):
 # dram__bytes_write.sum from one ncu capture of the current kernel on each
 # workload (the commands are in profiles/); None where the kernel has changed
 # since its last capture
-TRAFFIC = {"c1": None, "c1l": None}
+TRAFFIC = {"c1": None, "c1l": None, "c1_resident": None}
 
 
-def roofline_record(s, info, step_ms, workload, b_F=4):
+def roofline_record(s, info, step_ms, workload, b_F=4, kernel=None):
+    """Roofline of the kernel that advances the system one step: algorithmic
+    bytes of a step over its device time per step (for the resident kernel,
+    one launch's duration over the steps it ran)."""
     d = s.d
     Z = info["total_list_entries"] / s.N
     bpa = alg_bytes_per_atom_step(d, Z, b_F)
     achieved = bpa * s.N / (step_ms * 1e-3) / 1e9 if step_ms else None
     peak, peak_kind = peaks()
+    name = kernel or "k_step<%d,%s> (pair forces + kicks + drift + trigger, one launch per step)" % (
+        d, "mixed" if b_F == 4 else "fp64")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None,
-            "traffic": TRAFFIC.get(workload),
-            "kernel": "k_step<%d,%s> (pair forces + kicks + drift + trigger)"
-                      % (d, "mixed" if b_F == 4 else "fp64"),
+            "traffic": TRAFFIC.get(workload + ("_resident" if kernel else "")),
+            "kernel": name, "ms_per_step": step_ms,
             "bytes_per_atom_step": bpa, "N": s.N, "mean_list_length": Z,
             "design_bytes_per_atom_step": design_bytes_per_atom_step(d, Z),
             "peak_kind": peak_kind, "l2_bytes": l2_bytes(),
@@ -490,7 +494,12 @@ def run_gpu(args):
 
     d = s.d
     Z = info["total_list_entries"] / s.N
-    n_launch = args.steps * (md_per_step + 1) + 6 * rebuilds
+    if info.get("resident"):
+        # per bench step: first kick-drift, step budget, final force + kick;
+        # one resident launch per list, and the list builds (six kernels each)
+        n_launch = args.steps * 3 + (rebuilds + args.steps) + 6 * rebuilds
+    else:
+        n_launch = args.steps * (md_per_step + 1) + 6 * rebuilds
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -504,10 +513,17 @@ def run_gpu(args):
                    "l2": "flushed (512 MB write) before each timed step",
                    "n_cell": info["n_cell"], "mean_list_length": Z,
                    "lanes_per_atom": info["lanes_per_atom"], "graphs": info["graphs"],
+                   "resident_blocks": info.get("resident", 0),
                    "rebuilds_per_step": rebuilds / args.steps},
         "fp64": fp64,
         "kernel_ms": prof,
-        "roofline": roofline_record(s, info, prof["step_ms"] if prof else None, args.workload),
+        "roofline": (roofline_record(s, info, prof["resident_step_ms"], args.workload,
+                                     kernel="k_md_resident<%d> (resident MD: pair forces + kicks "
+                                            "+ drift + trigger, many steps per launch)" % d)
+                     if prof and prof.get("resident_step_ms") else
+                     roofline_record(s, info, prof["step_ms"] if prof else None, args.workload)),
+        "roofline_per_step_kernel": roofline_record(s, info, prof["step_ms"] if prof else None,
+                                                    args.workload) if prof else None,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * nd * 8,
                 "d2h_bytes_per_step": 2 * nd * 8 + 7 * 8},

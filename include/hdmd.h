@@ -304,11 +304,13 @@ hdmd_status set_resident(hdmd_system *sys, int on);
 /* Benchmark support, not part of the method: average device time in
  * milliseconds of single kernels on the current state, each launch timed
  * alone with a CUDA event pair on the system's stream and averaged over reps
- * launches.  ms_out[0]: the fused MD kernel (pair forces over the list, both
- * half kicks, drift, trigger reduction) with time step dt; ms_out[1]: one
- * full list build (wrap, binning, counting sort, reorder, Verlet lists);
- * ms_out[2]: the force-only kernel.  The state (positions, velocities,
- * lists) is restored before returning. */
+ * launches.  ms_out (host, 4 doubles)[0]: the fused MD kernel (pair forces
+ * over the list, both half kicks, drift, trigger reduction) with time step
+ * dt; [1]: one full list build (wrap, binning, counting sort, reorder,
+ * Verlet lists); [2]: the force-only kernel; [3]: the resident MD kernel,
+ * one launch of up to 20 reps steps divided by the steps it ran (0 where
+ * md_steps would not use it).  The state (positions, velocities, lists) is
+ * restored before returning. */
 hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_out);
 
 /* Forces, pair energy and virial of N harmonic spheres, for callers that

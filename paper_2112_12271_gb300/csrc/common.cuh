@@ -29,6 +29,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 // Streaming (evict-first) loads and stores for the per-atom data a step reads
 // and writes once; HDMD_STREAM_HINTS=0 builds them as plain accesses.
@@ -200,9 +201,56 @@ __host__ __device__ constexpr int pow3(int d) { return d <= 0 ? 1 : 3 * pow3(d -
 // integer pipe instead of the narrow FP64 pipe of this GPU.  Both follow the
 // standard's definitions: binary32 -> binary64 is exact; binary64 -> binary32
 // rounds to nearest, ties to even, with overflow to infinity and gradual
-// underflow to subnormals; NaN stays NaN.
-__device__ __forceinline__ double f32_to_f64(float f) {
-    const uint32_t u = __float_as_uint(f);
+// underflow to subnormals; NaN stays NaN.  Host-callable too, so that a CPU
+// test can hold them against the host's own conversions.
+__host__ __device__ __forceinline__ uint32_t bits_f32(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float f32_bits(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ uint64_t bits_f64(double x) {
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t u;
+    memcpy(&u, &x, 8);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ double f64_bits(uint64_t u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+__host__ __device__ __forceinline__ int lead_zeros32(uint32_t m) {
+#ifdef __CUDA_ARCH__
+    return __clz(m);
+#else
+    int k = 0;
+    while (k < 32 && !(m & (0x80000000u >> k))) ++k;
+    return k;
+#endif
+}
+
+__host__ __device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = bits_f32(f);
     const uint32_t sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
     uint32_t hi, lo;
     if (e != 0u && e != 0xffu) {               // normal: rebias 127 -> 1023
@@ -215,37 +263,38 @@ __device__ __forceinline__ double f32_to_f64(float f) {
         hi = sign;
         lo = 0u;
     } else {                                   // subnormal: normalise
-        const int k = __clz(m) - 8;            // shifts that bring bit 23 up
+        const int k = lead_zeros32(m) - 8;     // shifts that bring bit 23 up
         const uint32_t mn = (m << k) & 0x7fffffu;
         hi = sign | ((uint32_t)(897 - k) << 20) | (mn >> 3);
         lo = mn << 29;
     }
-    return __hiloint2double((int)hi, (int)lo);
+    return f64_bits(((uint64_t)hi << 32) | lo);
 }
 
-__device__ __forceinline__ float f64_to_f32(double x) {
-    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+__host__ __device__ __forceinline__ float f64_to_f32(double x) {
+    const uint64_t bx = bits_f64(x);
+    const uint32_t hi = (uint32_t)(bx >> 32), lo = (uint32_t)bx;
     const uint32_t sign = hi & 0x80000000u;
     const int e = (int)((hi >> 20) & 0x7ffu);
     const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the kept 23 bits
     const uint32_t rest = lo & 0x1fffffffu;                      // the 29 dropped bits
     if (e == 0x7ff)                                              // infinity, NaN
-        return __uint_as_float(sign | 0x7f800000u | m23 | ((m23 | rest) ? 0x400000u : 0u));
+        return f32_bits(sign | 0x7f800000u | m23 | ((m23 | rest) ? 0x400000u : 0u));
     const int ef = e - 896;
     if (ef >= 1) {
-        if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+        if (ef >= 255) return f32_bits(sign | 0x7f800000u);
         uint32_t r = sign | ((uint32_t)ef << 23) | m23;
         r += (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
-        return __uint_as_float(r);   // a carry into the exponent is the rounded value
+        return f32_bits(r);   // a carry into the exponent is the rounded value
     }
     // binary32 subnormal or zero: significand with its leading 1, shifted
-    if (e == 0) return __uint_as_float(sign);   // binary64 zero or subnormal: below 2^-1022
+    if (e == 0) return f32_bits(sign);   // binary64 zero or subnormal: below 2^-1022
     const uint64_t M = ((uint64_t)(0x100000u | (hi & 0xfffffu)) << 32) | lo;   // 53 bits
     const int sh = 926 - e;                     // >= 30
-    if (sh >= 64) return __uint_as_float(sign);
+    if (sh >= 64) return f32_bits(sign);
     const uint64_t q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
     const uint32_t r = (uint32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
-    return __uint_as_float(sign | r);
+    return f32_bits(sign | r);
 }
 
 #ifndef HDMD_INT_CVT

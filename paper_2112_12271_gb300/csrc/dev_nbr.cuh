@@ -325,4 +325,211 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
     }
 }
 
+// Lists of every atom of home subcell c (one warp; n_cell >= 3), the home
+// atoms staged in shared memory (sh: 32 x home_row_floats(D) floats of this
+// warp) and read by broadcast, the lanes carrying candidates: each candidate
+// is tested against all home atoms that reach its row (the expanded test of
+// nbr_batch, branch-free), and only a chunk with a hit takes the vote and the
+// compaction.  Home atoms beyond 32 are taken in further passes.  Entries come
+// out in the order of nbr_batch: rows, then pieces, then candidates.
+__host__ __device__ constexpr int home_row_floats(int D) { return (D + 2 + 3) & ~3; }
+
+template <int D>
+__device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *sh) {
+    constexpr int RF = Rows<D>::RF, HR = home_row_floats(D);
+    const int cs = dv.cell_start[c], ce = dv.cell_start[c + 1];
+    const int n = dv.n;
+    int C[D];
+    {
+        int t = c;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) { C[k] = t % n; t /= n; }
+    }
+    const float Lsc = dv.Lsc_f, hLsc = 0.5f * dv.Lsc_f;
+    const float skin = (float)dv.skin;
+    const bool glob = dv.rglobal_f > 0.f;
+    const float band_abs = 1e-5f * Lsc * Lsc;
+    const float reach_pad = dv.hmax_f;
+    const float rcmax = 2.f * dv.hmax_f + skin;
+    const float band_x = fmaf(1e-5f, rcmax * rcmax, band_abs)
+                       + (float)((D + 3) * (4 * D + 1)) * 1.2e-7f * Lsc * Lsc;
+    const int Srow = pow_int(3, D - 1);
+    const int cl = C[D - 1];
+    const int cl_m = cl == 0 ? n - 1 : cl - 1, cl_p = cl == n - 1 ? 0 : cl + 1;
+
+    for (int h0 = cs; h0 < ce; h0 += 32) {
+        const int nh = min(32, ce - h0);
+        const unsigned allh = nh == 32 ? 0xffffffffu : (1u << nh) - 1u;
+        // stage the home atoms: coordinates, list radius, |x|^2 - rho^2
+        __syncwarp();
+        if (lane < nh) {
+            const float *ri = dv.gs0 + (size_t)(h0 + lane) * RF;
+            float *hr = sh + lane * HR;
+            const float rh = (glob ? dv.hmax_f : ri[D]) + skin;
+            float b = -rh * rh;   // the order of nbr_batch: the same rounding
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                hr[k] = ri[k];
+                b = fmaf(ri[k], ri[k], b);
+            }
+            hr[D] = rh;
+            hr[D + 1] = b;
+        }
+        __syncwarp();
+        int cnt = 0;   // list length of home atom h0 + lane
+
+        for (int sr0 = 0; sr0 < Srow; sr0 += 32) {
+            // lane: row sr0 + lane of the stencil (offsets of axes 0..D-2),
+            // which home atoms reach it, and its pieces along the last axis
+            const int sr = sr0 + lane;
+            int Jrow = 0;
+            uint32_t rcode = 0;
+            unsigned amask = 0, mlo = 0, mhi = 0;
+            int ps1 = 0, pl1 = 0, ps2 = 0, pl2 = 0, ps3 = 0, pl3 = 0;
+            if (sr < Srow) {
+                int off[D];
+                int rem = sr;
+#pragma unroll
+                for (int k = D - 2; k >= 0; --k) { off[k] = rem % 3 - 1; rem /= 3; }
+#pragma unroll
+                for (int k = 0; k < D - 1; ++k) {
+                    int cj = C[k] + off[k];
+                    cj = cj < 0 ? cj + n : (cj >= n ? cj - n : cj);
+                    Jrow = Jrow * n + cj;
+                    rcode |= (uint32_t)(off[k] + 1) << (2 * k);
+                }
+                Jrow *= n;
+                for (int h = 0; h < nh; ++h) {
+                    const float *hr = sh + h * HR;
+                    float b2 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D - 1; ++k) {
+                        float dk = off[k] > 0 ? hLsc - hr[k] : (off[k] < 0 ? hr[k] + hLsc : 0.f);
+                        dk = fmaxf(dk, 0.f);
+                        b2 = fmaf(dk, dk, b2);
+                    }
+                    const float reach = (hr[D] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
+                    const float r2 = reach * reach;
+                    const float dlo = fmaxf(hr[D - 1] + hLsc, 0.f), dhi = fmaxf(hLsc - hr[D - 1], 0.f);
+                    if (b2 < r2) amask |= 1u << h;
+                    if (fmaf(dlo, dlo, b2) < r2) mlo |= 1u << h;
+                    if (fmaf(dhi, dhi, b2) < r2) mhi |= 1u << h;
+                }
+                if (amask) {   // a piece no home atom reaches along the last axis is skipped
+                    ps1 = dv.cell_start[Jrow + cl_m]; pl1 = mlo ? dv.cell_start[Jrow + cl_m + 1] - ps1 : 0;
+                    ps2 = dv.cell_start[Jrow + cl];   pl2 = dv.cell_start[Jrow + cl + 1] - ps2;
+                    ps3 = dv.cell_start[Jrow + cl_p]; pl3 = mhi ? dv.cell_start[Jrow + cl_p + 1] - ps3 : 0;
+                }
+            }
+            unsigned rows = __ballot_sync(0xffffffffu, amask != 0);
+            while (rows) {
+                const int src = __ffs(rows) - 1;
+                rows &= rows - 1;
+                const uint32_t rc0 = __shfl_sync(0xffffffffu, rcode, src);
+                const unsigned active = __shfl_sync(0xffffffffu, amask, src);
+                float offL[D];
+#pragma unroll
+                for (int k = 0; k < D - 1; ++k) offL[k] = code_offset(rc0, k) * Lsc;
+                const int s1 = __shfl_sync(0xffffffffu, ps1, src), l1 = __shfl_sync(0xffffffffu, pl1, src);
+                const int s2 = __shfl_sync(0xffffffffu, ps2, src), l2 = __shfl_sync(0xffffffffu, pl2, src);
+                const int s3 = __shfl_sync(0xffffffffu, ps3, src), l3 = __shfl_sync(0xffffffffu, pl3, src);
+                const int tot = l1 + l2 + l3;
+                for (int t0 = 0; t0 < tot; t0 += 32) {
+                    const int t = t0 + lane;
+                    const bool okj = t < tot;
+                    int j, olast;
+                    if (t < l1) { j = s1 + t; olast = -1; }
+                    else if (t < l1 + l2) { j = s2 + (t - l1); olast = 0; }
+                    else { j = s3 + (t - l1 - l2); olast = 1; }
+                    if (!okj) { j = s1 < dv.N ? s1 : 0; olast = -1; }
+                    float rj[RF];
+                    {
+                        const float4 *rj4 = reinterpret_cast<const float4 *>(dv.gs0 + (size_t)j * RF);
+#pragma unroll
+                        for (int q = 0; q < RF / 4; ++q) {
+                            const float4 tt = __ldg(rj4 + q);
+                            rj[4 * q] = tt.x; rj[4 * q + 1] = tt.y; rj[4 * q + 2] = tt.z; rj[4 * q + 3] = tt.w;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < D - 1; ++k) rj[k] += offL[k];
+                    rj[D - 1] = fmaf((float)olast, Lsc, rj[D - 1]);
+                    const float rhoj = glob ? dv.hmax_f : rj[D];
+                    float Aj = -rhoj * rhoj;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) Aj = fmaf(rj[k], rj[k], Aj);
+                    // every reaching home atom, branch-free (warp-uniform loop)
+                    unsigned hits = 0u, close = 0u;
+                    for (unsigned act = active; act; act &= act - 1u) {
+                        const int h = __ffs(act) - 1;
+                        float hx[HR];
+                        const float4 *hr4 = reinterpret_cast<const float4 *>(sh + h * HR);
+#pragma unroll
+                        for (int q = 0; q < HR / 4; ++q) {
+                            const float4 tt = hr4[q];
+                            hx[4 * q] = tt.x; hx[4 * q + 1] = tt.y; hx[4 * q + 2] = tt.z; hx[4 * q + 3] = tt.w;
+                        }
+                        float da = rhoj * hx[D], db = 0.f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            if (k & 1) db = fmaf(rj[k], hx[k], db);
+                            else da = fmaf(rj[k], hx[k], da);
+                        }
+                        const float diff = fmaf(-2.f, da + db, Aj + hx[D + 1]);
+                        hits |= (diff < -band_x ? 1u : 0u) << h;
+                        close |= (fabsf(diff) <= band_x ? 1u : 0u) << h;
+                    }
+                    const unsigned self = (unsigned)(j - h0) < (unsigned)nh ? 1u << (j - h0) : 0u;
+                    const unsigned cand = okj ? (active & ~self) : 0u;
+                    hits &= cand;
+                    close &= cand;
+                    while (close) {   // FP64 decision (positions are x0 at a build)
+                        const int h = __ffs(close) - 1;
+                        close &= close - 1;
+                        const int i = h0 + h;
+                        double s2d = 0.0;
+                        for (int k = 0; k < D; ++k) {
+                            double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
+                            dx -= dv.L * rint(dx * dv.invL);
+                            s2d += dx * dx;
+                        }
+                        const double rcd = glob ? dv.rglobal : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
+                        if (s2d < rcd * rcd) hits |= 1u << h;
+                    }
+                    unsigned any = __reduce_or_sync(0xffffffffu, hits);
+                    if (!any) continue;
+                    const uint32_t wcode = rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)));
+                    while (any) {   // home atoms in order; candidates in lane order
+                        const int h = __ffs(any) - 1;
+                        any &= any - 1u;
+                        const bool hit = (hits >> h) & 1u;
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        const int base = __shfl_sync(0xffffffffu, cnt, h);
+                        if (hit) {
+                            const int idx = base + __popc(m & ((1u << lane) - 1u));
+                            if (idx < dv.cap) {
+                                const int64_t pos = list_pos(idx, h0 + h, dv.Npad, dv.lgG);
+                                if (dv.pack_sh) {
+                                    dv.nbr[pos] = (int32_t)pack_entry<D>(dv, j, wcode);
+                                } else {
+                                    dv.nbr[pos] = j;
+                                    dv.code[pos] = wcode;
+                                }
+                            }
+                        }
+                        if (lane == h) cnt += __popc(m);
+                    }
+                }
+            }
+        }
+        if (lane < nh) {
+            const int i = h0 + lane;
+            dv.nnbr[i] = min(cnt, dv.cap);
+            if (cnt > dv.cap) atomicOr(&dv.flags->error, (int)ERR_OVERFLOW);
+            atomicMax(&dv.flags->max_count, cnt);
+            atomicAdd((unsigned long long *)&dv.flags->total_entries, (unsigned long long)cnt);
+        }
+    }
+}
+
 }  // namespace hdmd

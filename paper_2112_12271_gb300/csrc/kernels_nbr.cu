@@ -57,15 +57,32 @@ k_nbr_build(Dev dv, bool guarded) {
     nbr_batch<D, WRAP, nbr_allh(D)>(dv, w, threadIdx.x & 31);
 }
 
+// n_cell >= 3: one warp per home subcell, its atoms staged in shared memory
+// (nbr_cell)
+#ifndef HDMD_NBR_CELL_MIN_BLOCKS
+#define HDMD_NBR_CELL_MIN_BLOCKS 8
+#endif
+template <int D>
+__global__ void __launch_bounds__(NT, HDMD_NBR_CELL_MIN_BLOCKS) k_nbr_cell(Dev dv, bool guarded) {
+    __shared__ __align__(16) float sh[(NT / 32) * 32 * home_row_floats(D)];
+    if (guarded && *((volatile int *)&dv.flags->rebuild) == 0) return;
+    const int warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * (NT / 32) + warp;
+    if (c >= dv.ncells) return;   // warp-uniform; no block barrier follows
+    nbr_cell<D>(dv, c, threadIdx.x & 31, sh + warp * 32 * home_row_floats(D));
+}
+
 template <int D>
 void nbr_impl(const Dev &dv, bool guarded, cudaStream_t s) {
+    if (dv.n >= 3) {
+        const int blocks = (dv.ncells + NT / 32 - 1) / (NT / 32);
+        k_nbr_cell<D><<<blocks, NT, 0, s>>>(dv, guarded);
+        return;
+    }
     // upper bound on the number of home batches: N / H + n_cells
     const int64_t warps = (int64_t)dv.N / home_batch(D) + dv.ncells + 1;
     const int blocks = (int)((warps * 32 + NT - 1) / NT);
-    if (dv.n >= 3)
-        k_nbr_build<D, true><<<blocks, NT, 0, s>>>(dv, guarded);
-    else
-        k_nbr_build<D, false><<<blocks, NT, 0, s>>>(dv, guarded);
+    k_nbr_build<D, false><<<blocks, NT, 0, s>>>(dv, guarded);
 }
 
 }  // namespace

@@ -1773,6 +1773,28 @@ hdmd_status profile_kernels(hdmd_system *sys, int reps, double dt, double *ms_ou
     });
     ms_out[1] = timed([&](int) { launch_rebuild(sys->dv, cur, false, sys->stream); });
     ms_out[2] = timed([&](int) { force_only(sys, cur, fp64, false); });
+    // the resident kernel: one launch of up to 20 reps steps (it stops early
+    // when the trigger fires), its duration over the steps it ran
+    ms_out[3] = 0.0;
+    ResPlan pl;
+    if (resident_plan(sys, &pl)) {
+        const long long want = 20LL * reps;
+        launch_set_res_left(sys->dv, want, sys->stream);
+        ResCfg rc = resident_cfg(sys, pl, cur, dt);
+        cudaEventRecord(ev[0], sys->stream);
+        cudaError_t e = launch_md_resident(sys->dv, rc, pl.grid, pl.smem, sys->stream);
+        cudaEventRecord(ev[1], sys->stream);
+        if (e == cudaSuccess) {
+            cudaStreamSynchronize(sys->stream);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            st = read_flags(sys);
+            const long long ran = want - sys->h_flags->res_left;
+            if (!st && ran > 0) ms_out[3] = (double)ms / (double)ran;
+        } else {
+            cudaGetLastError();
+        }
+    }
     for (auto &e : ev) cudaEventDestroy(e);
     CKL(sys);
     st = snapshot(sys, true);

@@ -346,10 +346,11 @@ def set_tuning(h, lanes_per_atom=0, use_graphs=-1):
 
 
 def profile_kernels(h, reps=50, dt=0.005):
-    """Average device ms of (fused MD kernel, full list build, force-only kernel)."""
-    out = np.zeros(3)
+    """Average device ms of (fused MD kernel, full list build, force-only
+    kernel, resident MD kernel per step)."""
+    out = np.zeros(4)
     _check(lib().profile_kernels(h, int(reps), float(dt), _p(out)), h)
-    return dict(step_ms=out[0], rebuild_ms=out[1], force_ms=out[2])
+    return dict(step_ms=out[0], rebuild_ms=out[1], force_ms=out[2], resident_step_ms=out[3])
 
 
 def destroy_system(h):
