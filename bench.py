@@ -364,29 +364,36 @@ def c3_record(hdmd, stream, jobs=512, max_iter=20000):
 
 
 def c4_record(serve_seconds=2.0, slots=16, small_n=1024, budget=256, pool_gb=2, policy="sjf",
-              seq_sample=24, time_limit=300.0):
+              seq_sample=24, time_limit=300.0, batch_work=None, resident=False, compare=True,
+              rate=200.0):
     """A fixed slice of the serving stream (the first serve_seconds of the
     Poisson arrivals at 200 requests/s): jobs/s and p50/p99 latency through
     the continuous-batching server, beside the first seq_sample requests
     served one after another as plain FP64 systems and by the server."""
     from paper_2112_12271_gb300 import serve
     from paper_2112_12271_gb300 import hdmd
-    reqs = W.c4_requests(duration=serve_seconds, rate=200.0, seed=0)
+    reqs = W.c4_requests(duration=serve_seconds, rate=rate, seed=0)
     systems = [W.c4_system(r) for r in reqs]
     warm = W.c4_requests(duration=0.05, rate=200.0, seed=1)
     kw = dict(precision=hdmd.HDMD_MIXED, slots=slots, small_N=small_n,
-              batch_pool_bytes=pool_gb << 30, budget=budget, policy=policy)
+              batch_pool_bytes=pool_gb << 30, budget=budget, policy=policy,
+              batch_work=batch_work, resident=resident)
     srv = serve.Server(**kw)
     srv.run(warm, [W.c4_system(r) for r in warm])
     summ = serve.summarize(srv.run(reqs, systems, time_limit=time_limit))
     srv.close()
     k = min(seq_sample, len(reqs))
-    seq = serve.summarize(serve.sequential_fp64(reqs[:k], systems[:k]))
-    srv2 = serve.Server(**kw)
-    sub = serve.summarize(srv2.run(reqs[:k], systems[:k]))
-    srv2.close()
+    seq = sub = None
+    if compare:
+        seq = serve.summarize(serve.sequential_fp64(reqs[:k], systems[:k]))
+        srv2 = serve.Server(**kw)
+        sub = serve.summarize(srv2.run(reqs[:k], systems[:k]))
+        srv2.close()
     return {"workload": "serve_poisson200_md_fire_d3-8_N256-131072",
-            "slice": "first %.1f s of arrivals (%d requests)" % (serve_seconds, len(reqs)),
+            "routing": {"small_N": small_n, "batch_work": batch_work, "slots": slots,
+                        "budget": budget, "system_jobs_resident": resident},
+            "slice": "first %.1f s of arrivals at %.0f requests/s (%d requests)"
+                     % (serve_seconds, rate, len(reqs)),
             "value": summ["jobs_per_s"], "unit": "jobs/s", "latency_p50_s": summ["p50_s"],
             "latency_p99_s": summ["p99_s"], "summary": summ, "policy": policy,
             "first_%d_requests" % k: {"server": sub, "sequential_fp64": seq}}
@@ -538,6 +545,11 @@ def run_gpu(args):
         line["c4_serving"] = c4_record(policy=args.policy, slots=args.slots,
                                        small_n=args.small_n, budget=args.budget,
                                        pool_gb=args.pool_gb)
+        # the same request mix offered below the server's capacity (~15
+        # jobs/s): latency of service rather than of the queue
+        line["c4_serving_below_capacity"] = c4_record(
+            serve_seconds=10.0, rate=10.0, policy=args.policy, slots=args.slots,
+            small_n=args.small_n, budget=args.budget, pool_gb=args.pool_gb, compare=False)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"], line["cpu_baseline_serial"] = cpu_baselines(s)
     print(json.dumps(line), flush=True)

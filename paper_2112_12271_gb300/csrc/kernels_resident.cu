@@ -22,6 +22,8 @@
 // state goes back to global memory and, inside a CUDA graph, the loop and
 // rebuild conditionals are set.  The arithmetic of a step is that of k_step,
 // so an NVE trajectory has the same bits as the one-launch-per-step path.
+#include <mutex>
+
 #include "dev_force.cuh"
 #include "launch.h"
 
@@ -386,10 +388,35 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
     }
 }
 
+// The kernel's dynamic shared-memory limit, raised once per device to all
+// that the device allows beside the kernel's static arrays (and never
+// lowered), under a lock: systems on several host threads launch the same
+// kernel with different sizes, and a per-launch setting would race.
+template <int D, int LAW, bool PACK>
+cudaError_t ensure_smem_limit() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_md_resident<D, LAW, PACK>);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_md_resident<D, LAW, PACK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
 template <int D, int LAW, bool PACK>
 cudaError_t launch_one(const Dev &dv, const ResCfg &rc, int grid, size_t smem, cudaStream_t s) {
     auto kern = k_md_resident<D, LAW, PACK>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit<D, LAW, PACK>();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -407,7 +434,7 @@ cudaError_t launch_one(const Dev &dv, const ResCfg &rc, int grid, size_t smem, c
 template <int D, int LAW, bool PACK>
 cudaError_t occupancy_one(size_t smem, int *blocks_per_sm) {
     auto kern = k_md_resident<D, LAW, PACK>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit<D, LAW, PACK>();
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, RT, smem);
 }

@@ -6,7 +6,11 @@ resident on the GPU until it finishes, and jobs that arrive while others run
 are admitted as soon as a slot and device memory free up, so their work
 overlaps on the device:
 
-* a job with N > small_N runs as its own system (``hdmd.System``, the
+* jobs are routed by estimated work (``work``: atom-steps, FIRE counted at
+  a typical iteration count): a job of at most ``batch_work`` atom-steps and
+  at most ``small_N`` atoms joins the batched engine, every other job runs
+  as its own system;
+* a system job runs as its own system (``hdmd.System``, the
   grid-wide kernels and CUDA graphs) on its own CUDA stream, in one of
   ``slots`` worker threads.  It is admitted (first come first served, or
   with policy "sjf" smallest estimated work first) when a slot is free and
@@ -14,7 +18,7 @@ overlaps on the device:
   head-room for list growth) fits in what the running systems leave of the
   device-memory budget (by default 85 % of the free HBM at start, less the
   batch pool);
-* a job with N <= small_N joins the batched engine (``hdmd.Batch``, one
+* a batched job joins the batched engine (``hdmd.Batch``, one
   thread block per job): a batch thread admits it when the engine's device
   pool has room for its arrays and launches the persistent kernels, each
   launch advancing every resident job by at most ``budget`` steps or FIRE
@@ -72,10 +76,15 @@ class Server:
     def __init__(self, precision=hdmd.HDMD_MIXED, slots=16, small_N=1024,
                  batch_pool_bytes=2 << 30, max_batch_jobs=2048, mem_bytes=None,
                  budget=256, dt=0.005, max_iter=20000, keep_positions=False,
-                 headroom=1.5, log=None, policy="fifo"):
+                 headroom=1.5, log=None, policy="fifo", batch_work=None, resident=False):
         if policy not in ("fifo", "sjf"):
             raise ValueError("policy must be 'fifo' or 'sjf'")
         self.policy = policy
+        # no work limit given: route by size alone
+        self.batch_work = float("inf") if batch_work is None else float(batch_work)
+        # system jobs share the GPU: the resident MD kernel holds whole SMs
+        # for a list's lifetime, which the other jobs would wait behind
+        self.resident = resident
         import torch
         self.torch = torch
         self.precision = precision
@@ -97,6 +106,10 @@ class Server:
         self._local = threading.local()
         self._lock = threading.Lock()
 
+    def to_batch(self, req):
+        """True when the request goes to the batched engine."""
+        return req["N"] <= self.small_N and work(req) <= self.batch_work
+
     # ------------------------------------------------------------ system jobs
     def _system_job(self, rec, system):
         torch = self.torch
@@ -106,6 +119,7 @@ class Server:
         req = rec.req
         with hdmd.System(system.d, system.L, system.sigma, system.x, system.v,
                          precision=self.precision, stream=s.cuda_stream) as g:
+            g.resident(self.resident)
             if req["kind"] == hdmd.JOB_MD:
                 t = g.md_steps(req["nsteps"], self.dt)
                 res = dict(status=hdmd.JOB_DONE, E_pair=t["E_pair"], K=t["K"],
@@ -176,7 +190,7 @@ class Server:
                 while pending and requests[pending[0]]["t"] <= now:
                     rec = recs[pending.popleft()]
                     rec.arrival = rec.req["t"]
-                    if rec.req["N"] <= self.small_N:
+                    if self.to_batch(rec.req):
                         small_q.append(rec)
                     elif self.policy == "sjf":   # keep the waiting systems by estimated work
                         big_q.append(rec)

@@ -33,6 +33,7 @@ class Tracker:
         self.running_at_start = []
         self.batch_added = []    # N of each batched job, in admission order
         self.batch_peak = 0
+        self.resident = []       # resident-kernel switch of each system job
 
 
 class FakeStream:
@@ -58,6 +59,9 @@ def fakes(tracker, batch_capacity=64):
             with tracker.lock:
                 tracker.running -= 1
             return False
+
+        def resident(self, on=True):
+            tracker.resident.append(bool(on))
 
         def md_steps(self, n, dt):
             time.sleep(JOB_S)
@@ -270,3 +274,21 @@ def test_summarize():
     assert s["p50_s"] == pytest.approx(np.percentile(lat, 50))
     assert s["p99_s"] == pytest.approx(np.percentile(lat, 99))
     assert s["batch_jobs"] == 1 and s["system_jobs"] == 2
+
+
+def test_routing_by_estimated_work(patched):
+    """A job joins the batched engine when it has at most small_N atoms and
+    at most batch_work estimated atom-steps (FIRE at its typical iteration
+    count, 500); every other job runs as a system, with the resident MD
+    kernel off (system jobs share the GPU)."""
+    tr = patched()
+    Ns = [1000, 1001, 3000, 6000]
+    reqs, systems = jobs(Ns, kinds=[0, 0, 1, 1], nsteps=[1000, 5000, 0, 0])
+    # work: 1e6 (batch), 5.005e6 (system), 1.5e6 (batch), N > small_N (system)
+    srv = server(small_N=5000, batch_work=2e6)
+    assert [srv.to_batch(r) for r in reqs] == [True, False, True, False]
+    recs = srv.run(reqs, systems, time_limit=20.0)
+    srv.close()
+    assert [r.path for r in recs] == ["batch", "system", "batch", "system"]
+    assert sorted(tr.batch_added) == [1000, 3000]
+    assert tr.resident == [False, False]
