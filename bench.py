@@ -256,11 +256,14 @@ def design_bytes_per_atom_step(d, Z):
     return 8.0 * Z + 4 + 16 * d + 16 * d + 3 * 4 * RF
 
 
-# DRAM bytes per launch of the fused step kernel, dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the current kernel on each
-# workload (the commands are in profiles/); None where the kernel has changed
-# since its last capture
-TRAFFIC = {"c1": None, "c1l": None, "c1_resident": None}
+# DRAM bytes per step of the kernel the roofline names, dram__bytes_read.sum
+# + dram__bytes_write.sum from one ncu capture of the current kernel (the
+# commands are in profiles/); None where no capture of the current kernel
+# exists.  c1_resident: 9.88 MB for one resident launch, which ran ~36 steps
+# (11 launches over 396 steps in the captured run), so ~0.27 MB per step.
+# c1l: the per-step kernel at N = 2^20 moved 416.7 MB per launch (397 B per
+# atom), scaled to N = 2^21 by the atom count.
+TRAFFIC = {"c1": None, "c1_resident": 9.882e6 / 36.0, "c1l": 416.72e6 * 2.0}
 
 
 def roofline_record(s, info, step_ms, workload, b_F=4, kernel=None):
