@@ -60,6 +60,9 @@ constexpr int kStepNT = HDMD_STEP_NT;   // threads per block of the force / upda
 constexpr int kMaxLanes = 32;      // largest lanes-per-atom group
 constexpr int kResNT = 1024;       // threads per block of the resident MD kernel
 constexpr int kResMaxGrid = 1024;  // most blocks of the resident MD kernel
+// step words of the resident MD kernel, one per 128-byte line: every block
+// polls every word each step, and words that share a line queue on it
+constexpr int kResWordStride = 16;
 
 // reduction slots
 enum Red {
@@ -295,6 +298,40 @@ __host__ __device__ __forceinline__ float f64_to_f32(double x) {
     const uint64_t q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
     const uint32_t r = (uint32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
     return f32_bits(sign | r);
+}
+
+// One FP32 row (RF floats, RF * 4-byte aligned, allocations 256-byte aligned)
+// into registers.  A row of 8 floats is one 32-byte sector: one 256-bit load
+// per lane, so a warp's gather of 32 scattered rows costs the L1 one tag
+// look-up per row instead of two.  NC: the rows do not change while the
+// kernel runs (non-coherent read-only path); otherwise they are read from L2
+// (.cg), because other blocks rewrite them during the kernel.
+#ifndef HDMD_ROW_V8
+#define HDMD_ROW_V8 1
+#endif
+template <int RF, bool NC>
+__device__ __forceinline__ void load_row(const float *p, float (&r)[RF]) {
+#if HDMD_ROW_V8
+    if constexpr (RF == 8) {
+        if constexpr (NC)
+            asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]),
+                  "=f"(r[7])
+                : "l"(p));
+        else
+            asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]),
+                           "=f"(r[6]), "=f"(r[7])
+                         : "l"(p));
+        return;
+    }
+#endif
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int q = 0; q < RF / 4; ++q) {
+        const float4 t = NC ? __ldg(p4 + q) : __ldcg(p4 + q);
+        r[4 * q] = t.x; r[4 * q + 1] = t.y; r[4 * q + 2] = t.z; r[4 * q + 3] = t.w;
+    }
 }
 
 #ifndef HDMD_INT_CVT

@@ -186,16 +186,8 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
             }
             float rj[U][RF];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const float4 *rj4 = reinterpret_cast<const float4 *>(
-                    dv.gs[in_buf] + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF);
-#pragma unroll
-                for (int q = 0; q < RF / 4; ++q) {
-                    const float4 t = __ldg(rj4 + q);
-                    rj[u][4 * q] = t.x; rj[u][4 * q + 1] = t.y;
-                    rj[u][4 * q + 2] = t.z; rj[u][4 * q + 3] = t.w;
-                }
-            }
+            for (int u = 0; u < U; ++u)
+                load_row<RF, true>(dv.gs[in_buf] + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF, rj[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (jv[u] < 0) continue;

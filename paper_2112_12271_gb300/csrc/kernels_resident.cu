@@ -10,10 +10,12 @@
 // neighbours (through L2: ld.global.cg, since other blocks rewrite them every
 // step) and writes its own atoms' new rows:
 //   phase A  pair forces over the list (the FP32 pair path of dev_force.cuh,
-//            same lanes, entry order and lane sums as the grid kernel);
+//            same lanes per atom, entry order and lane sums as the grid
+//            kernel; the atoms taken longest list first);
 //   phase B  the merged kicks (v += dt F/m, or the Berendsen form) and the
-//            drift dlt += dt v in FP64, new rows gs0 + (float) dlt;
-//   phase C  rows out, per-atom |dlt|^2 summed in axis order, the block's
+//            drift dlt += dt v in FP64 over (atom, axis) items, new rows
+//            gs0 + (float) dlt out;
+//   phase C  per-atom |dlt|^2 summed in axis order, the block's
 //            maximum (and its NVT partial sum m v^2) published in a step word.
 // Blocks wait for every block's word of the step (bounded spins: a wait that
 // runs out sets ERR_TIMEOUT and the kernel returns), so every block sees the
@@ -87,15 +89,7 @@ __device__ __forceinline__ void res_forces(const Dev &dv, const float *__restric
         }
         float rj[U][RF];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const float4 *rj4 = reinterpret_cast<const float4 *>(gin + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF);
-#pragma unroll
-            for (int q = 0; q < RF / 4; ++q) {
-                const float4 t = __ldcg(rj4 + q);
-                rj[u][4 * q] = t.x; rj[u][4 * q + 1] = t.y;
-                rj[u][4 * q + 2] = t.z; rj[u][4 * q + 3] = t.w;
-            }
-        }
+        for (int u = 0; u < U; ++u) load_row<RF, false>(gin + (size_t)(jv[u] >= 0 ? jv[u] : i) * RF, rj[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (jv[u] < 0) continue;
@@ -132,14 +126,15 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
     const int na = i1 - i0, nc = rc.na_cap;
     const int G = dv.G, lgG = dv.lgG, Np = dv.Npad;
 
-    double *sV = reinterpret_cast<double *>(smem);            // [D][nc]
-    double *sDl = sV + (size_t)D * nc;                        // [D][nc]
+    double *sV = reinterpret_cast<double *>(smem);            // [nc][D]
+    double *sDl = sV + (size_t)D * nc;                        // [nc][D]
     double *sIm = sDl + (size_t)D * nc;                       // [nc]
     float *sRow = reinterpret_cast<float *>(sIm + nc + (nc & 1));   // [nc][RF] current rows (16-B aligned)
     float *sG0 = sRow + (size_t)nc * RF;                      // [nc][RF] build-time rows
     float *sF = sG0 + (size_t)nc * RF;                        // [nc][D] forces, then (float) dlt
     int *sOff = reinterpret_cast<int *>(sF + (size_t)nc * D); // [nc + 1] list offsets
-    uint32_t *sTab = reinterpret_cast<uint32_t *>(sOff + nc + 1);   // [3^D] codes (PACK)
+    int *sOrd = sOff + nc + 1;                                // [nc] atoms by list length
+    uint32_t *sTab = reinterpret_cast<uint32_t *>(sOrd + nc);       // [3^D] codes (PACK)
     uint32_t *sList = sTab + (PACK ? pow3(D) : 0);                   // [list_cap]
     uint32_t *sCode = sList + rc.list_cap;                           // [list_cap] (!PACK)
 
@@ -159,8 +154,8 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
     for (int t = tid; t < na * D; t += RT) {
         const int k = t / na, a = t - k * na;
         const size_t o = (size_t)k * Np + i0 + a;
-        sV[(size_t)k * nc + a] = dv.v[o];
-        sDl[(size_t)k * nc + a] = dv.dlt[o];
+        sV[a * D + k] = dv.v[o];
+        sDl[a * D + k] = dv.dlt[o];
     }
     if (dv.inv_mass)
         for (int a = tid; a < na; a += RT) sIm[a] = dv.inv_mass[i0 + a];
@@ -169,6 +164,16 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
         for (int t = tid; t < na * RF; t += RT) {
             sRow[t] = gr[t];
             sG0[t] = g0[t];
+        }
+    }
+    if (RF > D) {
+        // the radius (and padding) of the rows in the other buffer: steps
+        // rewrite only the coordinates
+        float *go = dv.gs[rc.in_buf ^ 1] + (size_t)i0 * RF;
+        const float *g0 = dv.gs0 + (size_t)i0 * RF;
+        for (int t = tid; t < na * (RF - D); t += RT) {
+            const int a = t / (RF - D), c = D + (t - a * (RF - D));
+            go[a * RF + c] = g0[a * RF + c];
         }
     }
     if (PACK)
@@ -194,6 +199,19 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
         }
     }
     __syncthreads();
+    // lane order of phase A: the block's atoms by list length, longest first
+    // (ties by index), so that the atoms of a warp have lists of about the
+    // same length and few lanes idle at the end of the shortest ones; every
+    // atom keeps its own lanes and entry order, so its force has the same bits
+    for (int a = tid; a < na; a += RT) {
+        const int la = sOff[a + 1] - sOff[a];
+        int r = 0;
+        for (int q = 0; q < na; ++q) {
+            const int lq = sOff[q + 1] - sOff[q];
+            r += (lq > la) || (lq == la && q < a);
+        }
+        sOrd[r] = a;
+    }
     const bool in_smem = s_smem != 0;
     if (in_smem) {
         const int apr = RT >> lgG;
@@ -223,12 +241,14 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
         {
             const int apr = RT >> lgG;
             for (int a0 = 0; a0 < na; a0 += apr) {
-                const int a = a0 + (tid >> lgG), g = tid & (G - 1);
+                const int slot = a0 + (tid >> lgG), g = tid & (G - 1);
+                const bool live = slot < na;
+                const int a = live ? sOrd[slot] : 0;
                 float f[D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) f[k] = 0.f;
                 float e = 0.f, w = 0.f;
-                if (a < na) {
+                if (live) {
                     if (in_smem)
                         res_forces<D, float, LAW, PACK, true>(dv, gin, a, i0 + a, g, lgG, sRow, sOff, sList,
                                                               sCode, sTab, f, e, w);
@@ -240,55 +260,57 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
                 }
-                if (g == 0 && a < na) {
+                if (g == 0 && live) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) sF[a * D + k] = f[k];
                 }
             }
         }
         __syncthreads();
-        // ---- phase B: one thread per atom: the merged kicks and the drift
-        // (the arithmetic of k_step), the new row out, |dlt|^2 in axis order
+        // ---- phase B: the merged kicks (v += dt F/m, or the Berendsen form)
+        // and the drift in FP64 (the arithmetic of k_step), spread over the
+        // block's (atom, axis) items so that the slow FP64 pipe has every warp
+        // to issue from; (float) dlt replaces the force in sF, and the new row
+        // coordinate goes to sRow and straight out to the other row buffer
+        // (the stores drain while the phase runs)
         double kin = 0.0;
         unsigned mb = 0u;
         {
             const double lam = s_lam;
-            float *go = dv.gs[pout] + (size_t)i0 * RF;
             const bool masses = dv.inv_mass != nullptr;
-            for (int a = tid; a < na; a += RT) {
+            float *go = dv.gs[pout] + (size_t)i0 * RF;
+            for (int t = tid; t < na * D; t += RT) {
+                const int a = t / D, k = t - a * D;
                 const double im = masses ? sIm[a] : 1.0;
-                float row[RF];
-                float d2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const double F = to_f64(sF[a * D + k]);
-                    double Fm = F;
-                    if (masses) Fm = F * im;   // a branch: no multiply without masses
-                    double v = sV[(size_t)k * nc + a];
-                    if (nvt) {
-                        const double vf = (v + hdt * Fm) * lam;
-                        kin += vf * vf / im;
-                        v = vf + hdt * Fm;
-                    } else {
-                        v += dt * Fm;
-                    }
-                    const double dl = sDl[(size_t)k * nc + a] + dt * v;
-                    sDl[(size_t)k * nc + a] = dl;
-                    sV[(size_t)k * nc + a] = v;
-                    const float fl = to_f32(dl);
-                    d2 = fmaf(fl, fl, d2);
-                    row[k] = sG0[a * RF + k] + fl;
+                const double F = to_f64(sF[t]);
+                double Fm = F;
+                if (masses) Fm = F * im;   // a branch: no multiply without masses
+                double v = sV[t];
+                if (nvt) {
+                    const double vf = (v + hdt * Fm) * lam;
+                    kin += vf * vf / im;
+                    v = vf + hdt * Fm;
+                } else {
+                    v += dt * Fm;
                 }
-#pragma unroll
-                for (int k = D; k < RF; ++k) row[k] = sRow[a * RF + k];
-#pragma unroll
-                for (int q = 0; q < RF / 4; ++q) {
-                    const float4 r4 = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
-                    reinterpret_cast<float4 *>(sRow + (size_t)a * RF)[q] = r4;
-                    reinterpret_cast<float4 *>(go + (size_t)a * RF)[q] = r4;
-                }
-                mb = max(mb, __float_as_uint(d2));
+                const double dl = sDl[t] + dt * v;
+                sDl[t] = dl;
+                sV[t] = v;
+                const float fl = to_f32(dl);
+                sF[t] = fl;
+                const float r = sG0[a * RF + k] + fl;
+                sRow[a * RF + k] = r;
+                go[a * RF + k] = r;
             }
+        }
+        __syncthreads();
+        // ---- phase C: |dlt|^2 of each atom summed by one thread in axis
+        // order (the trigger repeats bit for bit)
+        for (int a = tid; a < na; a += RT) {
+            float d2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) d2 = fmaf(sF[a * D + k], sF[a * D + k], d2);
+            mb = max(mb, __float_as_uint(d2));
         }
         mb = __reduce_max_sync(0xffffffffu, mb);
         double ks = kin;
@@ -304,16 +326,17 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
         const int par = (int)(tick & 1u);
         if (tid == 0) {
             unsigned m = 0u;
-            double kb = 0.0;
-            for (int q = 0; q < RT / 32; ++q) {
-                m = max(m, s_wmax[q]);
-                kb += s_wsum[q];
+            for (int q = 0; q < RT / 32; ++q) m = max(m, s_wmax[q]);
+            if (nvt) {
+                // a chain of dependent FP64 adds (slow on this pipe): NVT only
+                double kb = 0.0;
+                for (int q = 0; q < RT / 32; ++q) kb += s_wsum[q];
+                rc.kin[(size_t)par * nb + b] = kb;
             }
-            if (nvt) rc.kin[(size_t)par * nb + b] = kb;
-            // the block's row stores (ordered before this thread by the
-            // barrier) become visible at GPU scope before the step word
-            __threadfence();
-            st_release_u64(rc.sync + (size_t)par * nb + b, ((unsigned long long)tick << 32) | m);
+            // a release at GPU scope: the block's row stores, ordered before
+            // this thread by the barrier above, become visible before the word
+            // (no separate fence: the release is cumulative over them)
+            st_release_u64(rc.sync + ((size_t)par * nb + b) * kResWordStride, ((unsigned long long)tick << 32) | m);
         }
         // ---- wait for every block's word of this step
         unsigned gm = 0u;
@@ -322,7 +345,7 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
             unsigned long long wv = 0ull;
             long long it = 0;
             for (;;) {
-                wv = ld_acquire_u64(rc.sync + (size_t)par * nb + c);
+                wv = ld_acquire_u64(rc.sync + ((size_t)par * nb + c) * kResWordStride);
                 if ((unsigned)(wv >> 32) == tick) break;
                 if (++it > rc.spin_limit) { to = 1; break; }
                 if (it > 64) __nanosleep(32);
@@ -331,9 +354,8 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
             // written before the word's release, so visible after its acquire
             if (nvt) s_kinv[c] = __ldcg(rc.kin + (size_t)par * nb + c);
         }
-        // every thread: later reads of other blocks' rows come after the
-        // words' acquires (the barrier below orders the two)
-        __threadfence();
+        // later reads of other blocks' rows, by any thread of the block, come
+        // after the words' acquires: the barrier below orders the two
         gm = __reduce_max_sync(0xffffffffu, gm);
         if (lane == 0) s_gmax[warp] = gm;
         to = __syncthreads_or(to);
@@ -365,8 +387,8 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
     for (int t = tid; t < na * D; t += RT) {
         const int k = t / na, a = t - k * na;
         const size_t o = (size_t)k * Np + i0 + a;
-        dv.v[o] = sV[(size_t)k * nc + a];
-        dv.dlt[o] = sDl[(size_t)k * nc + a];
+        dv.v[o] = sV[a * D + k];
+        dv.dlt[o] = sDl[a * D + k];
     }
     if (steps & 1) {
         float *go = dv.gs[rc.in_buf] + (size_t)i0 * RF;
@@ -470,7 +492,7 @@ void launch_set_res_left(const Dev &dv, long long nsteps, cudaStream_t s) {
 size_t resident_fixed_smem(int d, int na_cap, bool pack) {
     const size_t RF = kRowFloats(d);
     size_t b = (size_t)(na_cap + (na_cap & 1)) * (2 * d * 8 + 8) + (size_t)na_cap * RF * 4 * 2 + (size_t)na_cap * d * 4 +
-               (size_t)(na_cap + 1) * 4;
+               (size_t)(na_cap + 1) * 4 + (size_t)na_cap * 4;
     if (pack) b += (size_t)pow3(d) * 4;
     return b;
 }

@@ -85,7 +85,8 @@ struct ResCfg {
     int na_cap;            // atoms per block, at most (shared-memory layout)
     int list_cap;          // list words per block held in shared memory
     long long spin_limit;  // polls of a step word before ERR_TIMEOUT
-    unsigned long long *sync;   // [2][grid] step words (tick << 32 | max |dlt|^2 bits)
+    unsigned long long *sync;   // [2][grid] step words (tick << 32 | max |dlt|^2 bits),
+                                // kResWordStride words apart
     double *kin;                // [2][grid] NVT partial sums
     unsigned long long cond_loop, cond_rebuild;   // graph conditionals (0: none)
 };

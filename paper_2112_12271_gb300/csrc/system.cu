@@ -155,7 +155,7 @@ struct hdmd_system {
     // resident MD kernel (one cooperative launch per list; see kernels_resident.cu)
     int use_resident = 1;
     bool res_graph_ok = true;
-    unsigned long long *res_sync = nullptr;   // [2][kResMaxGrid] step words
+    unsigned long long *res_sync = nullptr;   // [2][kResMaxGrid] step words, kResWordStride apart
     double *res_kin = nullptr;                // [2][kResMaxGrid] NVT partials
     // SWAP buffers (allocated on first use)
     SwapDev sw{};
@@ -1187,7 +1187,7 @@ int64_t create_bytes(int d, int64_t N, int64_t ncells, int cap, int G) {
     SB(st_i, nd); SB(st_cnt, Np); SB(st_off, Np + 1);
     SB(snap_x0, nd); SB(snap_dlt, nd); SB(snap_v, nd); SB(snap_sig, Np);
     SB(snap_im, Np); SB(snap_img, nd); SB(snap_id, Np);
-    SB(res_sync, 2 * kResMaxGrid); SB(res_kin, 2 * kResMaxGrid);
+    SB(res_sync, 2 * kResMaxGrid * kResWordStride); SB(res_kin, 2 * kResMaxGrid);
 #undef FB
 #undef SB
     int64_t c = ((int64_t)(cap + G - 1) / G) * G;
@@ -1290,7 +1290,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
     DA2(sys->st_i, nd); DA2(sys->st_cnt, Np); DA2(sys->st_off, Np + 1);
     DA2(sys->snap_x0, nd); DA2(sys->snap_dlt, nd); DA2(sys->snap_v, nd); DA2(sys->snap_sig, Np);
     DA2(sys->snap_im, Np); DA2(sys->snap_img, nd); DA2(sys->snap_id, Np);
-    DA2(sys->res_sync, 2 * kResMaxGrid); DA2(sys->res_kin, 2 * kResMaxGrid);
+    DA2(sys->res_sync, 2 * kResMaxGrid * kResWordStride); DA2(sys->res_kin, 2 * kResMaxGrid);
 #undef DA2
     sys->h_flags = (Flags *)pinned_get();
     sys->h_red = (double *)pinned_get();
@@ -1305,7 +1305,7 @@ hdmd_status create_system(int d, int64_t N, double L, const double *diameters,
         return bail(fail(sys, HDMD_E_CUDA, "stream creation failed"));
     }
     if (cudaMemsetAsync(dv.flags, 0, sizeof(Flags), sys->stream) != cudaSuccess ||
-        cudaMemsetAsync(sys->res_sync, 0, sizeof(unsigned long long) * 2 * kResMaxGrid, sys->stream) != cudaSuccess ||
+        cudaMemsetAsync(sys->res_sync, 0, sizeof(unsigned long long) * 2 * kResMaxGrid * kResWordStride, sys->stream) != cudaSuccess ||
         cudaMemsetAsync(dv.cell_count, 0, sizeof(int32_t) * dv.ncells, sys->stream) != cudaSuccess ||
         cudaMemsetAsync(dv.nnbr, 0, sizeof(int32_t) * Np, sys->stream) != cudaSuccess) {
         cudaGetLastError();
