@@ -327,11 +327,15 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
 
 // Lists of every atom of home subcell c (one warp; n_cell >= 3), the home
 // atoms staged in shared memory (sh: 32 x home_row_floats(D) floats of this
-// warp) and read by broadcast, the lanes carrying candidates: each candidate
-// is tested against all home atoms that reach its row (the expanded test of
-// nbr_batch, branch-free), and only a chunk with a hit takes the vote and the
-// compaction.  Home atoms beyond 32 are taken in further passes.  Entries come
-// out in the order of nbr_batch: rows, then pieces, then candidates.
+// warp: -2 x_h, -2 rho_h and |x_h|^2 - rho_h^2, so that the test of a
+// candidate is one add and D + 1 fused multiply-adds) and read by broadcast,
+// the lanes carrying candidates: each candidate is tested against all home
+// atoms that reach its row (the expanded test of nbr_batch, branch-free) for
+// one mask of pairs inside the list radius or within the rounding band of it;
+// only those pairs are looked at again (band: FP64 decision), and only a
+// chunk with a hit takes the vote and the compaction.  Home atoms beyond 32
+// are taken in further passes.  Entries come out in the order of nbr_batch:
+// rows, then pieces, then candidates.
 __host__ __device__ constexpr int home_row_floats(int D) { return (D + 2 + 3) & ~3; }
 
 template <int D>
@@ -369,10 +373,10 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
             float b = -rh * rh;   // the order of nbr_batch: the same rounding
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                hr[k] = ri[k];
+                hr[k] = -2.f * ri[k];   // exact: a power of two
                 b = fmaf(ri[k], ri[k], b);
             }
-            hr[D] = rh;
+            hr[D] = -2.f * rh;
             hr[D + 1] = b;
         }
         __syncwarp();
@@ -404,13 +408,15 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
                     float b2 = 0.f;
 #pragma unroll
                     for (int k = 0; k < D - 1; ++k) {
-                        float dk = off[k] > 0 ? hLsc - hr[k] : (off[k] < 0 ? hr[k] + hLsc : 0.f);
+                        const float xk = -0.5f * hr[k];
+                        float dk = off[k] > 0 ? hLsc - xk : (off[k] < 0 ? xk + hLsc : 0.f);
                         dk = fmaxf(dk, 0.f);
                         b2 = fmaf(dk, dk, b2);
                     }
-                    const float reach = (hr[D] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
+                    const float reach = (-0.5f * hr[D] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
                     const float r2 = reach * reach;
-                    const float dlo = fmaxf(hr[D - 1] + hLsc, 0.f), dhi = fmaxf(hLsc - hr[D - 1], 0.f);
+                    const float xl = -0.5f * hr[D - 1];
+                    const float dlo = fmaxf(xl + hLsc, 0.f), dhi = fmaxf(hLsc - xl, 0.f);
                     if (b2 < r2) amask |= 1u << h;
                     if (fmaf(dlo, dlo, b2) < r2) mlo |= 1u << h;
                     if (fmaf(dhi, dhi, b2) < r2) mhi |= 1u << h;
@@ -458,10 +464,8 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
                     float Aj = -rhoj * rhoj;
 #pragma unroll
                     for (int k = 0; k < D; ++k) Aj = fmaf(rj[k], rj[k], Aj);
-                    // every reaching home atom, branch-free (warp-uniform loop)
-                    unsigned hits = 0u, close = 0u;
-                    for (unsigned act = active; act; act &= act - 1u) {
-                        const int h = __ffs(act) - 1;
+                    // |x_j - x_h|^2 - (rho_j + rho_h)^2 for home atom h
+                    auto gap = [&](int h) {
                         float hx[HR];
                         const float4 *hr4 = reinterpret_cast<const float4 *>(sh + h * HR);
 #pragma unroll
@@ -469,23 +473,27 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
                             const float4 tt = hr4[q];
                             hx[4 * q] = tt.x; hx[4 * q + 1] = tt.y; hx[4 * q + 2] = tt.z; hx[4 * q + 3] = tt.w;
                         }
-                        float da = rhoj * hx[D], db = 0.f;
+                        float t = fmaf(rhoj, hx[D], Aj + hx[D + 1]);
 #pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            if (k & 1) db = fmaf(rj[k], hx[k], db);
-                            else da = fmaf(rj[k], hx[k], da);
-                        }
-                        const float diff = fmaf(-2.f, da + db, Aj + hx[D + 1]);
-                        hits |= (diff < -band_x ? 1u : 0u) << h;
-                        close |= (fabsf(diff) <= band_x ? 1u : 0u) << h;
+                        for (int k = 0; k < D; ++k) t = fmaf(rj[k], hx[k], t);
+                        return t;
+                    };
+                    // every reaching home atom, branch-free (warp-uniform loop)
+                    unsigned maybe = 0u;
+                    for (unsigned act = active; act; act &= act - 1u) {
+                        const int h = __ffs(act) - 1;
+                        if (gap(h) <= band_x) maybe |= 1u << h;
                     }
                     const unsigned self = (unsigned)(j - h0) < (unsigned)nh ? 1u << (j - h0) : 0u;
-                    const unsigned cand = okj ? (active & ~self) : 0u;
-                    hits &= cand;
-                    close &= cand;
-                    while (close) {   // FP64 decision (positions are x0 at a build)
-                        const int h = __ffs(close) - 1;
-                        close &= close - 1;
+                    maybe &= okj ? ~self : 0u;
+                    unsigned hits = 0u;
+                    while (maybe) {   // a hit, or a pair in the band: FP64 decision (x0 at a build)
+                        const int h = __ffs(maybe) - 1;
+                        maybe &= maybe - 1;
+                        if (gap(h) < -band_x) {
+                            hits |= 1u << h;
+                            continue;
+                        }
                         const int i = h0 + h;
                         double s2d = 0.0;
                         for (int k = 0; k < D; ++k) {
