@@ -237,9 +237,22 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
     while (left > 0) {
         const int pin = rc.in_buf ^ (steps & 1), pout = pin ^ 1;
         const float *gin = dv.gs[pin];
-        // ---- phase A: pair forces
+        // ---- phases A and B, warp by warp: a warp's atoms (slots of the
+        // lane order) get their pair forces, and the same warp at once takes
+        // their merged kicks (v += dt F/m, or the Berendsen form) and drift in
+        // FP64 (the arithmetic of k_step) over (atom, axis) items, with no
+        // block barrier between: the slow FP64 pipe works beside the other
+        // warps' row gathers.  (float) dlt replaces the force in sF; the new
+        // row coordinate goes to sRow and straight out to the other row buffer.
+        // Then |dlt|^2 of each atom, summed by one lane in axis order (the
+        // trigger repeats bit for bit).
+        double kin = 0.0;
+        unsigned mb = 0u;
         {
-            const int apr = RT >> lgG;
+            const int apr = RT >> lgG, apw = 32 >> lgG;   // atom slots per pass, per warp
+            const double lam = s_lam;
+            const bool masses = dv.inv_mass != nullptr;
+            float *go = dv.gs[pout] + (size_t)i0 * RF;
             for (int a0 = 0; a0 < na; a0 += apr) {
                 const int slot = a0 + (tid >> lgG), g = tid & (G - 1);
                 const bool live = slot < na;
@@ -264,53 +277,42 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) sF[a * D + k] = f[k];
                 }
-            }
-        }
-        __syncthreads();
-        // ---- phase B: the merged kicks (v += dt F/m, or the Berendsen form)
-        // and the drift in FP64 (the arithmetic of k_step), spread over the
-        // block's (atom, axis) items so that the slow FP64 pipe has every warp
-        // to issue from; (float) dlt replaces the force in sF, and the new row
-        // coordinate goes to sRow and straight out to the other row buffer
-        // (the stores drain while the phase runs)
-        double kin = 0.0;
-        unsigned mb = 0u;
-        {
-            const double lam = s_lam;
-            const bool masses = dv.inv_mass != nullptr;
-            float *go = dv.gs[pout] + (size_t)i0 * RF;
-            for (int t = tid; t < na * D; t += RT) {
-                const int a = t / D, k = t - a * D;
-                const double im = masses ? sIm[a] : 1.0;
-                const double F = to_f64(sF[t]);
-                double Fm = F;
-                if (masses) Fm = F * im;   // a branch: no multiply without masses
-                double v = sV[t];
-                if (nvt) {
-                    const double vf = (v + hdt * Fm) * lam;
-                    kin += vf * vf / im;
-                    v = vf + hdt * Fm;
-                } else {
-                    v += dt * Fm;
+                __syncwarp();
+                const int s0 = a0 + warp * apw;   // this warp's first slot
+                for (int q = lane; q < apw * D; q += 32) {
+                    const int qa = q / D, k = q - qa * D;
+                    if (s0 + qa >= na) break;
+                    const int aa = sOrd[s0 + qa], t = aa * D + k;
+                    const double im = masses ? sIm[aa] : 1.0;
+                    const double F = to_f64(sF[t]);
+                    double Fm = F;
+                    if (masses) Fm = F * im;   // a branch: no multiply without masses
+                    double v = sV[t];
+                    if (nvt) {
+                        const double vf = (v + hdt * Fm) * lam;
+                        kin += vf * vf / im;
+                        v = vf + hdt * Fm;
+                    } else {
+                        v += dt * Fm;
+                    }
+                    const double dl = sDl[t] + dt * v;
+                    sDl[t] = dl;
+                    sV[t] = v;
+                    const float fl = to_f32(dl);
+                    sF[t] = fl;
+                    const float r = sG0[aa * RF + k] + fl;
+                    sRow[aa * RF + k] = r;
+                    go[aa * RF + k] = r;
                 }
-                const double dl = sDl[t] + dt * v;
-                sDl[t] = dl;
-                sV[t] = v;
-                const float fl = to_f32(dl);
-                sF[t] = fl;
-                const float r = sG0[a * RF + k] + fl;
-                sRow[a * RF + k] = r;
-                go[a * RF + k] = r;
-            }
-        }
-        __syncthreads();
-        // ---- phase C: |dlt|^2 of each atom summed by one thread in axis
-        // order (the trigger repeats bit for bit)
-        for (int a = tid; a < na; a += RT) {
-            float d2 = 0.f;
+                __syncwarp();
+                if (lane < apw && s0 + lane < na) {
+                    const int aa = sOrd[s0 + lane];
+                    float d2 = 0.f;
 #pragma unroll
-            for (int k = 0; k < D; ++k) d2 = fmaf(sF[a * D + k], sF[a * D + k], d2);
-            mb = max(mb, __float_as_uint(d2));
+                    for (int k = 0; k < D; ++k) d2 = fmaf(sF[aa * D + k], sF[aa * D + k], d2);
+                    mb = max(mb, __float_as_uint(d2));
+                }
+            }
         }
         mb = __reduce_max_sync(0xffffffffu, mb);
         double ks = kin;
