@@ -25,6 +25,7 @@
 // rebuild conditionals are set.  The arithmetic of a step is that of k_step,
 // so an NVE trajectory has the same bits as the one-launch-per-step path.
 #include <mutex>
+#include <type_traits>
 
 #include "dev_force.cuh"
 #include "launch.h"
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
     __shared__ double s_kinv[RT];   // the blocks' NVT partials of the step, by block
     __shared__ double s_wsum[RT / 32];
     __shared__ double s_lam;
-    __shared__ unsigned s_d2;
+    __shared__ int s_trig, s_lost;
     __shared__ int s_stop, s_tout, s_smem;
 
     const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
@@ -279,31 +280,40 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
                 }
                 __syncwarp();
                 const int s0 = a0 + warp * apw;   // this warp's first slot
-                for (int q = lane; q < apw * D; q += 32) {
-                    const int qa = q / D, k = q - qa * D;
-                    if (s0 + qa >= na) break;
-                    const int aa = sOrd[s0 + qa], t = aa * D + k;
-                    const double im = masses ? sIm[aa] : 1.0;
-                    const double F = to_f64(sF[t]);
-                    double Fm = F;
-                    if (masses) Fm = F * im;   // a branch: no multiply without masses
-                    double v = sV[t];
-                    if (nvt) {
-                        const double vf = (v + hdt * Fm) * lam;
-                        kin += vf * vf / im;
-                        v = vf + hdt * Fm;
-                    } else {
-                        v += dt * Fm;
+                // (two copies of the loop: without masses there is no multiply
+                // by 1/m at all, not even one the compiler might speculate)
+                auto items = [&](auto with_mass) {
+                    constexpr bool MASS = decltype(with_mass)::value;
+                    for (int q = lane; q < apw * D; q += 32) {
+                        const int qa = q / D, k = q - qa * D;
+                        if (s0 + qa >= na) break;
+                        const int aa = sOrd[s0 + qa], t = aa * D + k;
+                        const double F = to_f64(sF[t]);
+                        double Fm = F, im = 1.0;
+                        if constexpr (MASS) {
+                            im = sIm[aa];
+                            Fm = F * im;
+                        }
+                        double v = sV[t];
+                        if (nvt) {
+                            const double vf = (v + hdt * Fm) * lam;
+                            kin += vf * vf / im;
+                            v = vf + hdt * Fm;
+                        } else {
+                            v += dt * Fm;
+                        }
+                        const double dl = sDl[t] + dt * v;
+                        sDl[t] = dl;
+                        sV[t] = v;
+                        const float fl = to_f32(dl);
+                        sF[t] = fl;
+                        const float r = sG0[aa * RF + k] + fl;
+                        sRow[aa * RF + k] = r;
+                        go[aa * RF + k] = r;
                     }
-                    const double dl = sDl[t] + dt * v;
-                    sDl[t] = dl;
-                    sV[t] = v;
-                    const float fl = to_f32(dl);
-                    sF[t] = fl;
-                    const float r = sG0[aa * RF + k] + fl;
-                    sRow[aa * RF + k] = r;
-                    go[aa * RF + k] = r;
-                }
+                };
+                if (masses) items(std::true_type{});
+                else items(std::false_type{});
                 __syncwarp();
                 if (lane < apw && s0 + lane < na) {
                     const int aa = sOrd[s0 + lane];
@@ -364,8 +374,13 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
         if (tid == 0) {
             unsigned m = 0u;
             for (int q = 0; q < RT / 32; ++q) m = max(m, s_gmax[q]);
-            s_d2 = m;
             s_tout = to;
+            // the step's decision, taken once (the FP64 compare is slow on
+            // this pipe): the trigger 2 max|dlt| > s, and a lost atom
+            const float d2 = __uint_as_float(m);
+            const bool finite = d2 <= 3.0e38f;
+            s_trig = (4.0f * d2 > s2) || !finite;
+            s_lost = !finite || 16.0 * (double)d2 > dv.L * dv.L;
             if (nvt && !to) {
                 double k2 = 0.0;
                 for (int c = 0; c < nb; ++c) k2 += s_kinv[c];   // block order: the same sum everywhere
@@ -378,10 +393,8 @@ __global__ void __launch_bounds__(RT, 1) k_md_resident(Dev dv, ResCfg rc) {
         ++steps;
         --left;
         if (s_tout) { tout = 1; break; }
-        const float d2 = __uint_as_float(s_d2);
-        const bool finite = d2 <= 3.0e38f;
-        trig = (4.0f * d2 > s2) || !finite;
-        lost = !finite || 16.0 * (double)d2 > dv.L * dv.L;
+        trig = s_trig;
+        lost = s_lost;
         if (trig) break;
     }
 
