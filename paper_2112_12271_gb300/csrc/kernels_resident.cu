@@ -36,7 +36,7 @@ namespace {
 constexpr int RT = kResNT;
 
 #ifndef HDMD_RES_UNROLL
-#define HDMD_RES_UNROLL 3   // list entries in flight per lane
+#define HDMD_RES_UNROLL 2   // list entries in flight per lane (2, 3, 4 measured)
 #endif
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
