@@ -48,6 +48,33 @@ __device__ __forceinline__ T eps_pair(T eps, T hi, T hj, int scale) {
     return eps * q;
 }
 
+// The pair vector of one list entry in FP32: dx = x_i - x_j - o Lsc (o the
+// entry's subcell offsets from its code; x_i - x_j rounds once, the offset
+// term is exact and rounds once more), two axes per packed instruction, and
+// r2 = |dx|^2 summed in axis order (the bits of the scalar loop)
+template <int D>
+__device__ __forceinline__ float entry_dx(const float (&xi)[D], const float *rj, uint32_t code, float Lsc,
+                                          float (&dx)[D]) {
+    const float2 m1 = make_float2(-1.f, -1.f), mL = make_float2(-Lsc, -Lsc);
+    const float2 c0 = make_float2(-12582913.0f, -12582913.0f);   // see code_offset
+#pragma unroll
+    for (int p = 0; p < D / 2; ++p) {
+        const float2 ob = make_float2(__uint_as_float(0x4B400000u | ((code >> (4 * p)) & 3u)),
+                                      __uint_as_float(0x4B400000u | ((code >> (4 * p + 2)) & 3u)));
+        const float2 o = __fadd2_rn(ob, c0);
+        const float2 xr = __ffma2_rn(make_float2(rj[2 * p], rj[2 * p + 1]), m1,
+                                     make_float2(xi[2 * p], xi[2 * p + 1]));
+        const float2 t = __ffma2_rn(o, mL, xr);
+        dx[2 * p] = t.x;
+        dx[2 * p + 1] = t.y;
+    }
+    if (D & 1) dx[D - 1] = fmaf(-code_offset(code, D - 1), Lsc, xi[D - 1] - rj[D - 1]);
+    float r2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) r2 = fmaf(dx[k], dx[k], r2);
+    return r2;
+}
+
 // One pair's contribution in FP32 arithmetic: dx = x_i - x_j (minimum
 // image), r2 = |dx|^2, radii hi, hj (s = hi + hj is the contact distance);
 // adds the force on i to f, U to e and r.f to w when r < s.
@@ -191,15 +218,8 @@ __device__ __forceinline__ void pair_forces(const Dev &dv, int i, int g, int lgG
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (jv[u] < 0) continue;
-                const uint32_t code = cv[u];
-                float dx[D], r2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const float o = code_offset(code, k);
-                    const float t = fmaf(-o, Lsc, xi[k] - rj[u][k]);
-                    dx[k] = t;
-                    r2 = fmaf(t, t, r2);
-                }
+                float dx[D];
+                const float r2 = entry_dx<D>(xi, rj[u], cv[u], Lsc, dx);
                 pair_term_f32<D, FT, LAW>(dv, dx, r2, hi, rj[u][D], eps, ma, scale, f, e, w);
             }
         }

@@ -94,12 +94,11 @@ __device__ __forceinline__ void res_forces(const Dev &dv, const float *__restric
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (jv[u] < 0) continue;
-            const uint32_t code = cv[u];
+            // the scalar form of entry_dx (the same bits; measured faster here)
             float dx[D], r2 = 0.f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                const float o = code_offset(code, k);
-                const float t = fmaf(-o, Lsc, xi[k] - rj[u][k]);
+                const float t = fmaf(-code_offset(cv[u], k), Lsc, xi[k] - rj[u][k]);
                 dx[k] = t;
                 r2 = fmaf(t, t, r2);
             }
