@@ -259,11 +259,12 @@ def design_bytes_per_atom_step(d, Z):
 # DRAM bytes per step of the kernel the roofline names, dram__bytes_read.sum
 # + dram__bytes_write.sum from one ncu capture of the current kernel (the
 # commands are in profiles/); None where no capture of the current kernel
-# exists.  c1_resident: 9.88 MB for one resident launch, which ran ~36 steps
-# (11 launches over 396 steps in the captured run), so ~0.27 MB per step.
-# c1l: the per-step kernel at N = 2^20 moved 416.7 MB per launch (397 B per
-# atom), scaled to N = 2^21 by the atom count.
-TRAFFIC = {"c1": None, "c1_resident": 9.882e6 / 36.0, "c1l": 416.72e6 * 2.0}
+# exists.  c1_resident: 9.98 MB for one resident launch (ncu replays it with
+# cold caches, so this is the launch's load of the block state), which ran
+# ~36 steps (11 launches over 392 steps in the captured run): ~0.28 MB per
+# step.  c1l: the per-step kernel at N = 2^20 moved 417.6 MB per launch
+# (398 B per atom), scaled to N = 2^21 by the atom count.
+TRAFFIC = {"c1": None, "c1_resident": 9.980e6 / 36.0, "c1l": 417.61e6 * 2.0}
 
 
 def roofline_record(s, info, step_ms, workload, b_F=4, kernel=None):
