@@ -69,7 +69,10 @@ template <int D>
 __global__ void k_assign(Dev dv, bool guarded) {
     if (skip(dv, guarded)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < dv.N) assign_one<D>(dv, i);
+    if (i < dv.N) {
+        assign_one<D>(dv, i);
+        dv.nnbr[i] = 0;   // list counters of the half-stencil build (atomics)
+    }
 }
 
 // step 2: exclusive scans (one block) of the histogram -> cell_start, and of

@@ -75,6 +75,28 @@ def test_neighbor_lists_match_oracle(H, d, N, L):
             compare_lists(got, ref, ties)
 
 
+def test_half_stencil_lists_match_oracle_and_repeat(H):
+    """A system with many candidates per atom (3^d times the atoms per
+    subcell >= 4000: here d = 6, n_cell = 3, ~11 atoms per subcell) takes the
+    half-stencil build: each pair tested once and entered in both lists at
+    slots taken by atomics, then every list sorted by neighbour index.  The
+    sets equal the oracle's brute force, and a forced rebuild gives the same
+    lists and order bit for bit."""
+    rng = np.random.default_rng(7)
+    d, N, L = 6, 8192, 4.6
+    x = W.uniform_positions(rng, N, d, L)
+    sigma = W.polydisperse(rng, N)
+    ref = oracle.neighbors_brute(x, sigma, L, 0.3)
+    ties = tie_pairs(x, sigma, L, 0.3)
+    with H.System(d, L, sigma, x, precision=H.HDMD_MIXED) as g:
+        assert g.info()["n_cell"] == 3
+        a = g.neighbors()
+        compare_lists(a, ref, ties)
+        g.build_neighbors(force=True)
+        b = g.neighbors()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
 @pytest.mark.parametrize("lanes", [1, 2, 8, 32])
 def test_lanes_per_atom_layouts(H, lanes):
     s = W.c1_poly_d6(N=2048)
