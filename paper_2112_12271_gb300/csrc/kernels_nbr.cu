@@ -77,48 +77,90 @@ __global__ void __launch_bounds__(NT, HDMD_NBR_CELL_MIN_BLOCKS) k_nbr_cell(Dev d
 // entries arrived in the order of the atomics that placed them; the code word
 // travels with its entry), the counts clamped to the capacity, and the
 // longest list and the total number of entries reported (one atomic per
-// block).
+// block).  One warp per list: the lanes hold the entries (up to kFinishK per
+// lane), each entry's rank is the number of smaller neighbour indices
+// (distinct within a list) counted through shuffles, and every entry is
+// written back at its rank; longer lists are sorted by one lane.
+constexpr int kFinishK = 4;   // entries per lane: lists up to 128 sorted by the warp
 __global__ void __launch_bounds__(NT) k_list_finish(Dev dv, bool guarded) {
     __shared__ int smax[NT / 32];
     __shared__ unsigned long long ssum[NT / 32];
     if (guarded && *((volatile int *)&dv.flags->rebuild) == 0) return;
-    const int i = blockIdx.x * NT + threadIdx.x;
-    int raw = 0;
-    if (i < dv.N) {
-        raw = dv.nnbr[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (NT / 32);
+    const bool packed = dv.pack_sh > 0;
+    const uint32_t msk = packed ? dv.idx_mask : 0xffffffffu;
+    uint32_t *nb = reinterpret_cast<uint32_t *>(dv.nbr);
+    int mx = 0;
+    unsigned long long sm = 0;
+    for (int i = blockIdx.x * (NT / 32) + warp; i < dv.N; i += nwarps) {
+        const int raw = dv.nnbr[i];
         const int n = min(raw, dv.cap);
-        if (raw > dv.cap) atomicOr(&dv.flags->error, (int)ERR_OVERFLOW);
-        const bool packed = dv.pack_sh > 0;
-        const uint32_t msk = packed ? dv.idx_mask : 0xffffffffu;
-        uint32_t *nb = reinterpret_cast<uint32_t *>(dv.nbr);
-        for (int m = 1; m < n; ++m) {   // insertion sort (lists are short)
-            const int64_t pm = list_pos(m, i, dv.Npad, dv.lgG);
-            const uint32_t e = nb[pm], key = e & msk;
-            const uint32_t cd = packed ? 0u : dv.code[pm];
-            int k = m - 1;
-            for (; k >= 0; --k) {
-                const int64_t pk = list_pos(k, i, dv.Npad, dv.lgG);
-                const uint32_t ek = nb[pk];
-                if ((ek & msk) <= key) break;
-                const int64_t pk1 = list_pos(k + 1, i, dv.Npad, dv.lgG);
-                nb[pk1] = ek;
-                if (!packed) dv.code[pk1] = dv.code[pk];
+        mx = max(mx, raw);
+        sm += (unsigned long long)raw;
+        if (n <= 32 * kFinishK) {
+            uint32_t e[kFinishK], cd[kFinishK], key[kFinishK];
+#pragma unroll
+            for (int q = 0; q < kFinishK; ++q) {
+                const int m = q * 32 + lane;
+                e[q] = 0u;
+                cd[q] = 0u;
+                key[q] = 0xffffffffu;
+                if (m < n) {
+                    const int64_t pm = list_pos(m, i, dv.Npad, dv.lgG);
+                    e[q] = nb[pm];
+                    if (!packed) cd[q] = dv.code[pm];
+                    key[q] = e[q] & msk;
+                }
             }
-            const int64_t pk1 = list_pos(k + 1, i, dv.Npad, dv.lgG);
-            nb[pk1] = e;
-            if (!packed) dv.code[pk1] = cd;
+            int rank[kFinishK] = {};
+#pragma unroll
+            for (int q2 = 0; q2 < kFinishK; ++q2) {
+                if (q2 * 32 >= n) break;
+                const int cnt = min(32, n - q2 * 32);
+                for (int l2 = 0; l2 < cnt; ++l2) {
+                    const uint32_t k2 = __shfl_sync(0xffffffffu, key[q2], l2);
+#pragma unroll
+                    for (int q = 0; q < kFinishK; ++q) rank[q] += k2 < key[q];
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < kFinishK; ++q) {
+                if (q * 32 + lane < n) {
+                    const int64_t pr = list_pos(rank[q], i, dv.Npad, dv.lgG);
+                    nb[pr] = e[q];
+                    if (!packed) dv.code[pr] = cd[q];
+                }
+            }
+        } else if (lane == 0) {
+            for (int m = 1; m < n; ++m) {   // insertion sort by one lane
+                const int64_t pm = list_pos(m, i, dv.Npad, dv.lgG);
+                const uint32_t e = nb[pm], key = e & msk;
+                const uint32_t cd = packed ? 0u : dv.code[pm];
+                int k = m - 1;
+                for (; k >= 0; --k) {
+                    const int64_t pk = list_pos(k, i, dv.Npad, dv.lgG);
+                    const uint32_t ek = nb[pk];
+                    if ((ek & msk) <= key) break;
+                    const int64_t pk1 = list_pos(k + 1, i, dv.Npad, dv.lgG);
+                    nb[pk1] = ek;
+                    if (!packed) dv.code[pk1] = dv.code[pk];
+                }
+                const int64_t pk1 = list_pos(k + 1, i, dv.Npad, dv.lgG);
+                nb[pk1] = e;
+                if (!packed) dv.code[pk1] = cd;
+            }
         }
-        dv.nnbr[i] = n;
+        if (lane == 0) {
+            dv.nnbr[i] = n;
+            if (raw > dv.cap) atomicOr(&dv.flags->error, (int)ERR_OVERFLOW);
+        }
+        __syncwarp();
     }
-    int mx = raw;
-    unsigned long long sm = (unsigned long long)raw;
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        smax[threadIdx.x >> 5] = mx;
-        ssum[threadIdx.x >> 5] = sm;
+    if (lane == 0) {
+        smax[warp] = mx;
+        ssum[warp] = sm;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -149,7 +191,8 @@ void nbr_impl(const Dev &dv, bool guarded, cudaStream_t s) {
         const int blocks = (dv.ncells + NT / 32 - 1) / (NT / 32);
         if (half_stencil(dv, pow3(D))) {
             k_nbr_cell<D, true><<<blocks, NT, 0, s>>>(dv, guarded);
-            if (dv.N > 0) k_list_finish<<<(dv.N + NT - 1) / NT, NT, 0, s>>>(dv, guarded);
+            const int warps = (dv.N + 0) < 152 * 8 * (NT / 32) ? dv.N : 152 * 8 * (NT / 32);
+            if (dv.N > 0) k_list_finish<<<(warps + NT / 32 - 1) / (NT / 32), NT, 0, s>>>(dv, guarded);
         } else {
             k_nbr_cell<D, false><<<blocks, NT, 0, s>>>(dv, guarded);
         }
