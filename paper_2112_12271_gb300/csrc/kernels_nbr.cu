@@ -176,11 +176,11 @@ __global__ void __launch_bounds__(NT) k_list_finish(Dev dv, bool guarded) {
 // The half-stencil build where a home atom has many candidates (3^d times
 // the atoms per subcell): it tests each pair once but pays atomics for the
 // slots and a sort of every list.  Same-box build times, half / full
-// stencil: d=6 N=32768 (5832 candidates) 0.363 / 0.376 ms, N=2^21 (5832)
-// 10.5 / 14.9 ms, the paper's model at N=10^5: d=6 (17.8k) 1.62 / 1.75 ms,
-// d=5 (3.1k) 0.60 / 0.54 ms, d=4 (550) 0.28 / 0.21 ms, d=3 (100) 0.18 /
-// 0.16 ms.
-constexpr double kHalfStencilCandidates = 4000.0;
+// stencil: d=6 N=32768 (5832 candidates) 0.289 / 0.376 ms, N=2^21 (5832)
+// 10.7 / 14.9 ms, the paper's model at N=10^5: d=6 (17.8k) 1.29 / 1.75 ms,
+// d=5 (3.1k) 0.478 / 0.548 ms, d=4 (550) 0.249 / 0.217 ms, d=3 (100)
+// 0.189 / 0.156 ms.
+constexpr double kHalfStencilCandidates = 1500.0;
 inline bool half_stencil(const Dev &dv, int stencil) {
     return (double)stencil * (double)dv.N >= kHalfStencilCandidates * (double)dv.ncells;
 }
