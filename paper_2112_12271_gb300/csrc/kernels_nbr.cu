@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_list_finish(Dev dv, bool guarded) {
 
 // The half-stencil build where a home atom has many candidates (3^d times
 // the atoms per subcell): it tests each pair once but pays atomics for the
-// slots and a sort of every list.  Same-box build times, half / full
+// slots and a sort of every list.  Build times on one GB300, half / full
 // stencil: d=6 N=32768 (5832 candidates) 0.289 / 0.376 ms, N=2^21 (5832)
 // 10.7 / 14.9 ms, the paper's model at N=10^5: d=6 (17.8k) 1.29 / 1.75 ms,
 // d=5 (3.1k) 0.478 / 0.548 ms, d=4 (550) 0.249 / 0.217 ms, d=3 (100)
