@@ -336,9 +336,17 @@ __device__ __forceinline__ void nbr_batch(const Dev &dv, int w, int lane) {
 // chunk with a hit takes the vote and the compaction.  Home atoms beyond 32
 // are taken in further passes.  Entries come out in the order of nbr_batch:
 // rows, then pieces, then candidates.
+//
+// HALF (Newton's third law): a home subcell takes the rows of the stencil
+// whose first non-zero offset on axes 0..D-2 is positive, and of the row of
+// zero offsets the pieces at last-axis offsets 0 and +1, the home piece only
+// for the pairs i < j; each pair found is entered in both lists (offset o
+// for the home atom, -o for the candidate) at slots taken by atomics on the
+// counters (zeroed by the binning), and k_list_finish then sorts every list
+// by neighbour index and clamps the counts: the same lists, in index order.
 __host__ __device__ constexpr int home_row_floats(int D) { return (D + 2 + 3) & ~3; }
 
-template <int D>
+template <int D, bool HALF>
 __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *sh) {
     constexpr int RF = Rows<D>::RF, HR = home_row_floats(D);
     const int cs = dv.cell_start[c], ce = dv.cell_start[c + 1];
@@ -380,7 +388,7 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
             hr[D + 1] = b;
         }
         __syncwarp();
-        int cnt = 0;   // list length of home atom h0 + lane
+        int cnt = 0;   // list length of home atom h0 + lane (full stencil)
 
         for (int sr0 = 0; sr0 < Srow; sr0 += 32) {
             // lane: row sr0 + lane of the stencil (offsets of axes 0..D-2),
@@ -390,11 +398,17 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
             uint32_t rcode = 0;
             unsigned amask = 0, mlo = 0, mhi = 0;
             int ps1 = 0, pl1 = 0, ps2 = 0, pl2 = 0, ps3 = 0, pl3 = 0;
+            int sgn = 1;   // sign of the row's first non-zero offset (axes 0..D-2; HALF)
             if (sr < Srow) {
                 int off[D];
                 int rem = sr;
 #pragma unroll
                 for (int k = D - 2; k >= 0; --k) { off[k] = rem % 3 - 1; rem /= 3; }
+                if constexpr (HALF) {
+                    sgn = 0;
+#pragma unroll
+                    for (int k = 0; k < D - 1; ++k) sgn = sgn ? sgn : off[k];
+                }
 #pragma unroll
                 for (int k = 0; k < D - 1; ++k) {
                     int cj = C[k] + off[k];
@@ -421,219 +435,7 @@ __device__ __forceinline__ void nbr_cell(const Dev &dv, int c, int lane, float *
                     if (fmaf(dlo, dlo, b2) < r2) mlo |= 1u << h;
                     if (fmaf(dhi, dhi, b2) < r2) mhi |= 1u << h;
                 }
-                if (amask) {   // a piece no home atom reaches along the last axis is skipped
-                    ps1 = dv.cell_start[Jrow + cl_m]; pl1 = mlo ? dv.cell_start[Jrow + cl_m + 1] - ps1 : 0;
-                    ps2 = dv.cell_start[Jrow + cl];   pl2 = dv.cell_start[Jrow + cl + 1] - ps2;
-                    ps3 = dv.cell_start[Jrow + cl_p]; pl3 = mhi ? dv.cell_start[Jrow + cl_p + 1] - ps3 : 0;
-                }
-            }
-            unsigned rows = __ballot_sync(0xffffffffu, amask != 0);
-            while (rows) {
-                const int src = __ffs(rows) - 1;
-                rows &= rows - 1;
-                const uint32_t rc0 = __shfl_sync(0xffffffffu, rcode, src);
-                const unsigned active = __shfl_sync(0xffffffffu, amask, src);
-                float offL[D];
-#pragma unroll
-                for (int k = 0; k < D - 1; ++k) offL[k] = code_offset(rc0, k) * Lsc;
-                const int s1 = __shfl_sync(0xffffffffu, ps1, src), l1 = __shfl_sync(0xffffffffu, pl1, src);
-                const int s2 = __shfl_sync(0xffffffffu, ps2, src), l2 = __shfl_sync(0xffffffffu, pl2, src);
-                const int s3 = __shfl_sync(0xffffffffu, ps3, src), l3 = __shfl_sync(0xffffffffu, pl3, src);
-                const int tot = l1 + l2 + l3;
-                for (int t0 = 0; t0 < tot; t0 += 32) {
-                    const int t = t0 + lane;
-                    const bool okj = t < tot;
-                    int j, olast;
-                    if (t < l1) { j = s1 + t; olast = -1; }
-                    else if (t < l1 + l2) { j = s2 + (t - l1); olast = 0; }
-                    else { j = s3 + (t - l1 - l2); olast = 1; }
-                    if (!okj) { j = s1 < dv.N ? s1 : 0; olast = -1; }
-                    float rj[RF];
-                    {
-                        const float4 *rj4 = reinterpret_cast<const float4 *>(dv.gs0 + (size_t)j * RF);
-#pragma unroll
-                        for (int q = 0; q < RF / 4; ++q) {
-                            const float4 tt = __ldg(rj4 + q);
-                            rj[4 * q] = tt.x; rj[4 * q + 1] = tt.y; rj[4 * q + 2] = tt.z; rj[4 * q + 3] = tt.w;
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < D - 1; ++k) rj[k] += offL[k];
-                    rj[D - 1] = fmaf((float)olast, Lsc, rj[D - 1]);
-                    const float rhoj = glob ? dv.hmax_f : rj[D];
-                    float Aj = -rhoj * rhoj;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) Aj = fmaf(rj[k], rj[k], Aj);
-                    // |x_j - x_h|^2 - (rho_j + rho_h)^2 for home atom h
-                    auto gap = [&](int h) {
-                        float hx[HR];
-                        const float4 *hr4 = reinterpret_cast<const float4 *>(sh + h * HR);
-#pragma unroll
-                        for (int q = 0; q < HR / 4; ++q) {
-                            const float4 tt = hr4[q];
-                            hx[4 * q] = tt.x; hx[4 * q + 1] = tt.y; hx[4 * q + 2] = tt.z; hx[4 * q + 3] = tt.w;
-                        }
-                        float t = fmaf(rhoj, hx[D], Aj + hx[D + 1]);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) t = fmaf(rj[k], hx[k], t);
-                        return t;
-                    };
-                    // every reaching home atom, branch-free (warp-uniform loop)
-                    unsigned maybe = 0u;
-                    for (unsigned act = active; act; act &= act - 1u) {
-                        const int h = __ffs(act) - 1;
-                        if (gap(h) <= band_x) maybe |= 1u << h;
-                    }
-                    const unsigned self = (unsigned)(j - h0) < (unsigned)nh ? 1u << (j - h0) : 0u;
-                    maybe &= okj ? ~self : 0u;
-                    unsigned hits = 0u;
-                    while (maybe) {   // a hit, or a pair in the band: FP64 decision (x0 at a build)
-                        const int h = __ffs(maybe) - 1;
-                        maybe &= maybe - 1;
-                        if (gap(h) < -band_x) {
-                            hits |= 1u << h;
-                            continue;
-                        }
-                        const int i = h0 + h;
-                        double s2d = 0.0;
-                        for (int k = 0; k < D; ++k) {
-                            double dx = dv.x0[(size_t)k * dv.Npad + j] - dv.x0[(size_t)k * dv.Npad + i];
-                            dx -= dv.L * rint(dx * dv.invL);
-                            s2d += dx * dx;
-                        }
-                        const double rcd = glob ? dv.rglobal : 0.5 * (dv.sigma[i] + dv.sigma[j]) + dv.skin;
-                        if (s2d < rcd * rcd) hits |= 1u << h;
-                    }
-                    unsigned any = __reduce_or_sync(0xffffffffu, hits);
-                    if (!any) continue;
-                    const uint32_t wcode = rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)));
-                    while (any) {   // home atoms in order; candidates in lane order
-                        const int h = __ffs(any) - 1;
-                        any &= any - 1u;
-                        const bool hit = (hits >> h) & 1u;
-                        const unsigned m = __ballot_sync(0xffffffffu, hit);
-                        const int base = __shfl_sync(0xffffffffu, cnt, h);
-                        if (hit) {
-                            const int idx = base + __popc(m & ((1u << lane) - 1u));
-                            if (idx < dv.cap) {
-                                const int64_t pos = list_pos(idx, h0 + h, dv.Npad, dv.lgG);
-                                if (dv.pack_sh) {
-                                    dv.nbr[pos] = (int32_t)pack_entry<D>(dv, j, wcode);
-                                } else {
-                                    dv.nbr[pos] = j;
-                                    dv.code[pos] = wcode;
-                                }
-                            }
-                        }
-                        if (lane == h) cnt += __popc(m);
-                    }
-                }
-            }
-        }
-        if (lane < nh) {
-            const int i = h0 + lane;
-            dv.nnbr[i] = min(cnt, dv.cap);
-            if (cnt > dv.cap) atomicOr(&dv.flags->error, (int)ERR_OVERFLOW);
-            atomicMax(&dv.flags->max_count, cnt);
-            atomicAdd((unsigned long long *)&dv.flags->total_entries, (unsigned long long)cnt);
-        }
-    }
-}
-
-// Half-stencil form of nbr_cell (Newton's third law): a home subcell takes
-// the rows of the stencil whose first non-zero offset on axes 0..D-2 is
-// positive, and of the row of zero offsets the pieces at last-axis offsets 0
-// and +1, the home piece only for the pairs i < j; each pair found is
-// entered in both lists (offset o for the home atom, -o for the candidate)
-// at slots taken by atomics on the counters (zeroed by the binning), and
-// k_list_finish then sorts every list by neighbour index and clamps the
-// counts: the same lists as nbr_cell, in index order.
-template <int D>
-__device__ __forceinline__ void nbr_cell_half(const Dev &dv, int c, int lane, float *sh) {
-    constexpr int RF = Rows<D>::RF, HR = home_row_floats(D);
-    const int cs = dv.cell_start[c], ce = dv.cell_start[c + 1];
-    const int n = dv.n;
-    int C[D];
-    {
-        int t = c;
-#pragma unroll
-        for (int k = D - 1; k >= 0; --k) { C[k] = t % n; t /= n; }
-    }
-    const float Lsc = dv.Lsc_f, hLsc = 0.5f * dv.Lsc_f;
-    const float skin = (float)dv.skin;
-    const bool glob = dv.rglobal_f > 0.f;
-    const float band_abs = 1e-5f * Lsc * Lsc;
-    const float reach_pad = dv.hmax_f;
-    const float rcmax = 2.f * dv.hmax_f + skin;
-    const float band_x = fmaf(1e-5f, rcmax * rcmax, band_abs)
-                       + (float)((D + 3) * (4 * D + 1)) * 1.2e-7f * Lsc * Lsc;
-    const int Srow = pow_int(3, D - 1);
-    const int cl = C[D - 1];
-    const int cl_m = cl == 0 ? n - 1 : cl - 1, cl_p = cl == n - 1 ? 0 : cl + 1;
-
-    for (int h0 = cs; h0 < ce; h0 += 32) {
-        const int nh = min(32, ce - h0);
-        const unsigned allh = nh == 32 ? 0xffffffffu : (1u << nh) - 1u;
-        // stage the home atoms: coordinates, list radius, |x|^2 - rho^2
-        __syncwarp();
-        if (lane < nh) {
-            const float *ri = dv.gs0 + (size_t)(h0 + lane) * RF;
-            float *hr = sh + lane * HR;
-            const float rh = (glob ? dv.hmax_f : ri[D]) + skin;
-            float b = -rh * rh;   // the order of nbr_batch: the same rounding
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                hr[k] = -2.f * ri[k];   // exact: a power of two
-                b = fmaf(ri[k], ri[k], b);
-            }
-            hr[D] = -2.f * rh;
-            hr[D + 1] = b;
-        }
-        __syncwarp();
-
-        for (int sr0 = 0; sr0 < Srow; sr0 += 32) {
-            // lane: row sr0 + lane of the stencil (offsets of axes 0..D-2),
-            // which home atoms reach it, and its pieces along the last axis
-            const int sr = sr0 + lane;
-            int Jrow = 0;
-            uint32_t rcode = 0;
-            unsigned amask = 0, mlo = 0, mhi = 0;
-            int ps1 = 0, pl1 = 0, ps2 = 0, pl2 = 0, ps3 = 0, pl3 = 0;
-            int sgn = 0;   // sign of the row's first non-zero offset (axes 0..D-2)
-            if (sr < Srow) {
-                int off[D];
-                int rem = sr;
-#pragma unroll
-                for (int k = D - 2; k >= 0; --k) { off[k] = rem % 3 - 1; rem /= 3; }
-#pragma unroll
-                for (int k = 0; k < D - 1; ++k) sgn = sgn ? sgn : off[k];
-#pragma unroll
-                for (int k = 0; k < D - 1; ++k) {
-                    int cj = C[k] + off[k];
-                    cj = cj < 0 ? cj + n : (cj >= n ? cj - n : cj);
-                    Jrow = Jrow * n + cj;
-                    rcode |= (uint32_t)(off[k] + 1) << (2 * k);
-                }
-                Jrow *= n;
-                for (int h = 0; h < nh; ++h) {
-                    const float *hr = sh + h * HR;
-                    float b2 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < D - 1; ++k) {
-                        const float xk = -0.5f * hr[k];
-                        float dk = off[k] > 0 ? hLsc - xk : (off[k] < 0 ? xk + hLsc : 0.f);
-                        dk = fmaxf(dk, 0.f);
-                        b2 = fmaf(dk, dk, b2);
-                    }
-                    const float reach = (-0.5f * hr[D] + reach_pad) * (1.0f + 1e-5f) + 1e-5f;
-                    const float r2 = reach * reach;
-                    const float xl = -0.5f * hr[D - 1];
-                    const float dlo = fmaxf(xl + hLsc, 0.f), dhi = fmaxf(hLsc - xl, 0.f);
-                    if (b2 < r2) amask |= 1u << h;
-                    if (fmaf(dlo, dlo, b2) < r2) mlo |= 1u << h;
-                    if (fmaf(dhi, dhi, b2) < r2) mhi |= 1u << h;
-                }
-                if (sgn < 0) amask = 0;   // the mirror half of the stencil
+                if (sgn < 0) amask = 0;   // the mirror half of the stencil (HALF)
                 if (amask) {   // a piece no home atom reaches along the last axis is skipped
                     ps1 = dv.cell_start[Jrow + cl_m];
                     pl1 = (mlo && sgn > 0) ? dv.cell_start[Jrow + cl_m + 1] - ps1 : 0;
@@ -647,7 +449,7 @@ __device__ __forceinline__ void nbr_cell_half(const Dev &dv, int c, int lane, fl
                 rows &= rows - 1;
                 const uint32_t rc0 = __shfl_sync(0xffffffffu, rcode, src);
                 const unsigned active = __shfl_sync(0xffffffffu, amask, src);
-                const bool zrow = __shfl_sync(0xffffffffu, sgn, src) == 0;   // offsets 0 on axes 0..D-2
+                const bool zrow = HALF && __shfl_sync(0xffffffffu, sgn, src) == 0;   // offsets 0 on axes 0..D-2
                 float offL[D];
 #pragma unroll
                 for (int k = 0; k < D - 1; ++k) offL[k] = code_offset(rc0, k) * Lsc;
@@ -699,11 +501,15 @@ __device__ __forceinline__ void nbr_cell_half(const Dev &dv, int c, int lane, fl
                         const int h = __ffs(act) - 1;
                         if (gap(h) <= band_x) maybe |= 1u << h;
                     }
-                    // the home subcell itself: the pairs i < j only
                     unsigned keep = okj ? 0xffffffffu : 0u;
-                    if (zrow && olast == 0) {
-                        const int dj = j - h0;
-                        keep &= dj <= 0 ? 0u : (dj >= 32 ? 0xffffffffu : (1u << dj) - 1u);
+                    if constexpr (HALF) {
+                        // the home subcell itself: the pairs i < j only
+                        if (zrow && olast == 0) {
+                            const int dj = j - h0;
+                            keep &= dj <= 0 ? 0u : (dj >= 32 ? 0xffffffffu : (1u << dj) - 1u);
+                        }
+                    } else {
+                        if ((unsigned)(j - h0) < (unsigned)nh) keep &= ~(1u << (j - h0));   // not itself
                     }
                     maybe &= keep;
                     unsigned hits = 0u;
@@ -727,35 +533,43 @@ __device__ __forceinline__ void nbr_cell_half(const Dev &dv, int c, int lane, fl
                     unsigned any = __reduce_or_sync(0xffffffffu, hits);
                     if (!any) continue;
                     const uint32_t wcode = rc0 | ((uint32_t)(olast + 1) << (2 * (D - 1)));
-                    // the opposite offset: 2 - c in every 2-bit field (no borrows)
-                    const uint32_t ncode = (0xAAAAAAAAu & (uint32_t)((1ull << (2 * D)) - 1ull)) - wcode;
-                    // the candidate's own list: every home atom it hit, slots
-                    // taken by one atomic per candidate (order fixed afterwards)
-                    if (hits) {
-                        const int bj = atomicAdd(dv.nnbr + j, __popc(hits));
-                        int r = 0;
-                        for (unsigned hm = hits; hm; hm &= hm - 1u, ++r) {
-                            const int idx = bj + r;
-                            if (idx >= dv.cap) break;
-                            const int i = h0 + __ffs(hm) - 1;
-                            const int64_t pos = list_pos(idx, j, dv.Npad, dv.lgG);
-                            if (dv.pack_sh) {
-                                dv.nbr[pos] = (int32_t)pack_entry<D>(dv, i, ncode);
-                            } else {
-                                dv.nbr[pos] = i;
-                                dv.code[pos] = ncode;
+                    if constexpr (HALF) {
+                        // the candidate's own list: every home atom it hit (the
+                        // opposite offset: 2 - c in every 2-bit field, no borrows),
+                        // slots taken by one atomic per candidate (order fixed
+                        // afterwards)
+                        const uint32_t ncode = (0xAAAAAAAAu & (uint32_t)((1ull << (2 * D)) - 1ull)) - wcode;
+                        if (hits) {
+                            const int bj = atomicAdd(dv.nnbr + j, __popc(hits));
+                            int r = 0;
+                            for (unsigned hm = hits; hm; hm &= hm - 1u, ++r) {
+                                const int idx = bj + r;
+                                if (idx >= dv.cap) break;
+                                const int i = h0 + __ffs(hm) - 1;
+                                const int64_t pos = list_pos(idx, j, dv.Npad, dv.lgG);
+                                if (dv.pack_sh) {
+                                    dv.nbr[pos] = (int32_t)pack_entry<D>(dv, i, ncode);
+                                } else {
+                                    dv.nbr[pos] = i;
+                                    dv.code[pos] = ncode;
+                                }
                             }
                         }
                     }
-                    while (any) {   // the home atoms' lists: one atomic per home atom hit
+                    while (any) {   // home atoms in order; candidates in lane order
                         const int h = __ffs(any) - 1;
                         any &= any - 1u;
                         const bool hit = (hits >> h) & 1u;
                         const unsigned m = __ballot_sync(0xffffffffu, hit);
-                        const int lead = __ffs(m) - 1;
-                        int base = 0;
-                        if (lane == lead) base = atomicAdd(dv.nnbr + h0 + h, __popc(m));
-                        base = __shfl_sync(0xffffffffu, base, lead);
+                        int base;
+                        if constexpr (HALF) {   // slots from the list's counter
+                            const int lead = __ffs(m) - 1;
+                            base = 0;
+                            if (lane == lead) base = atomicAdd(dv.nnbr + h0 + h, __popc(m));
+                            base = __shfl_sync(0xffffffffu, base, lead);
+                        } else {
+                            base = __shfl_sync(0xffffffffu, cnt, h);
+                        }
                         if (hit) {
                             const int idx = base + __popc(m & ((1u << lane) - 1u));
                             if (idx < dv.cap) {
@@ -768,12 +582,19 @@ __device__ __forceinline__ void nbr_cell_half(const Dev &dv, int c, int lane, fl
                                 }
                             }
                         }
+                        if (!HALF && lane == h) cnt += __popc(m);
                     }
                 }
             }
         }
+        if (!HALF && lane < nh) {
+            const int i = h0 + lane;
+            dv.nnbr[i] = min(cnt, dv.cap);
+            if (cnt > dv.cap) atomicOr(&dv.flags->error, (int)ERR_OVERFLOW);
+            atomicMax(&dv.flags->max_count, cnt);
+            atomicAdd((unsigned long long *)&dv.flags->total_entries, (unsigned long long)cnt);
+        }
     }
 }
-
 
 }  // namespace hdmd

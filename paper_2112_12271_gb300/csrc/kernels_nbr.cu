@@ -69,8 +69,7 @@ __global__ void __launch_bounds__(NT, HDMD_NBR_CELL_MIN_BLOCKS) k_nbr_cell(Dev d
     const int warp = threadIdx.x >> 5;
     const int c = blockIdx.x * (NT / 32) + warp;
     if (c >= dv.ncells) return;   // warp-uniform; no block barrier follows
-    if constexpr (HALF) nbr_cell_half<D>(dv, c, threadIdx.x & 31, sh + warp * 32 * home_row_floats(D));
-    else nbr_cell<D>(dv, c, threadIdx.x & 31, sh + warp * 32 * home_row_floats(D));
+    nbr_cell<D, HALF>(dv, c, threadIdx.x & 31, sh + warp * 32 * home_row_floats(D));
 }
 
 // After the half-stencil build: every list sorted by neighbour index (its
