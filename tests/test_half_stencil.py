@@ -1,7 +1,7 @@
 """Host checks of the half-stencil list build's rules (paper Sec. II.C: the
 3^d linked subcells of a home subcell), replayed on the CPU.
 
-The device builder (`nbr_cell_half` in csrc/dev_nbr.cuh) walks, for each home
+The device builder (`nbr_cell<D, true>` in csrc/dev_nbr.cuh) walks, for each home
 subcell, the stencil rows (offsets on axes 0..d-2) whose first non-zero
 offset is positive, all three pieces along the last axis; of the row of zero
 offsets only the pieces at last-axis offset 0 (pairs i < j) and +1.  Each
