@@ -505,12 +505,16 @@ def run_gpu(args):
 
     d = s.d
     Z = info["total_list_entries"] / s.N
+    # kernels of one list build: five of binning, the list kernel, and the
+    # sort of the lists where the half-stencil form applies (n_cell >= 3 and
+    # at least 1500 candidates per atom, the library's rule)
+    per_build = 6 + (1 if info["n_cell"] >= 3 and 3 ** d * s.N >= 1500 * info["n_cells"] else 0)
     if info.get("resident"):
         # per bench step: first kick-drift, step budget, final force + kick;
-        # one resident launch per list, and the list builds (six kernels each)
-        n_launch = args.steps * 3 + (rebuilds + args.steps) + 6 * rebuilds
+        # one resident launch per list, and the list builds
+        n_launch = args.steps * 3 + (rebuilds + args.steps) + per_build * rebuilds
     else:
-        n_launch = args.steps * (md_per_step + 1) + 6 * rebuilds
+        n_launch = args.steps * (md_per_step + 1) + per_build * rebuilds
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
