@@ -267,6 +267,14 @@ def design_bytes_per_atom_step(d, Z):
 TRAFFIC = {"c1": None, "c1_resident": 9.980e6 / 36.0, "c1l": 417.61e6 * 2.0}
 
 
+def list_build_kernels(d, N, n_cell, n_cells):
+    """Kernels one list build launches: five of binning, the list kernel, and
+    the sort of the lists where the half-stencil form applies (n_cell >= 3
+    and at least 1500 candidates per atom, 3^d times the atoms per subcell:
+    the library's rule)."""
+    return 6 + (1 if n_cell >= 3 and 3 ** d * N >= 1500 * n_cells else 0)
+
+
 def roofline_record(s, info, step_ms, workload, b_F=4, kernel=None):
     """Roofline of the kernel that advances the system one step: algorithmic
     bytes of a step over its device time per step (for the resident kernel,
@@ -505,10 +513,7 @@ def run_gpu(args):
 
     d = s.d
     Z = info["total_list_entries"] / s.N
-    # kernels of one list build: five of binning, the list kernel, and the
-    # sort of the lists where the half-stencil form applies (n_cell >= 3 and
-    # at least 1500 candidates per atom, the library's rule)
-    per_build = 6 + (1 if info["n_cell"] >= 3 and 3 ** d * s.N >= 1500 * info["n_cells"] else 0)
+    per_build = list_build_kernels(d, s.N, info["n_cell"], info["n_cells"])
     if info.get("resident"):
         # per bench step: first kick-drift, step budget, final force + kick;
         # one resident launch per list, and the list builds

@@ -121,3 +121,14 @@ def test_threaded_oracle_gives_the_serial_trajectory():
     assert a["builds"] == b["builds"] >= 2
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
     assert b["E"] == pytest.approx(a["E"], rel=1e-12)
+
+
+def test_list_build_kernel_count():
+    """The launch count of one list build: seven kernels where the half-stencil
+    build adds its list sort (d = 6 at N = 32768, n_cell 4; the paper's model at
+    d = 5), six elsewhere (the paper's model at d = 3 and 4; n_cell <= 2)."""
+    assert bench.list_build_kernels(6, 32768, 4, 4 ** 6) == 7
+    assert bench.list_build_kernels(5, 100000, 6, 6 ** 5) == 7
+    assert bench.list_build_kernels(4, 100000, 11, 11 ** 4) == 6
+    assert bench.list_build_kernels(3, 100000, 30, 30 ** 3) == 6
+    assert bench.list_build_kernels(6, 300, 2, 2 ** 6) == 6
